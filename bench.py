@@ -1,0 +1,310 @@
+"""Benchmark: OT solves/s of PINS on one GB300 (Algorithm 2, whole solve per step).
+
+Workload (default): a single dense instance, m = n = 4096, points from an
+8-component 2-D Gaussian mixture (means U[0,1]^2, sigma 0.05), squared-Euclidean
+cost normalised to max 1, a, b ~ Dirichlet(1), eta = 1e-2, the paper's
+hyperparameters (T1 = 100, T2 = 50, K = 250, Theorem 2 sparsity budget).  One
+step = one complete solve, the cost matrix already resident in HBM.  `e2e` times
+the same solve through the public C ABI from pinned host buffers (cost matrix
+and marginals uploaded, potentials read back) every step.
+
+Prints one JSON line (see the repository's benchmark contract).  `--impl
+reference` times the FP64 CPU oracle instead on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--eta", type=float, default=1e-2)
+    ap.add_argument("--K", type=int, default=250)
+    ap.add_argument("--gamma", type=float, default=1.0)
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="plain FP64 solves timed for the comparison key (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit())
+        mx = max(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def workload(args):
+    from paper_2502_03749_gb300 import workloads as wl
+    return wl.gmm_instance(0, m=args.n, n=args.n, eta=args.eta)
+
+
+def config_dict(args, w):
+    return {"workload": f"dense GMM instance m=n={args.n}, squared-Euclidean cost /max, "
+                        f"Dirichlet(1) marginals, eta={args.eta}",
+            "m": args.n, "n": args.n, "eta": args.eta, "K": args.K, "T1": 100, "T2": 50,
+            "sparsify_gamma": args.gamma, "precision": args.prec,
+            "l2_note": "C is 64 MiB FP32 (mixed) / 128 MiB FP64: larger than or close to the "
+                       "126 MiB L2; no flush between steps",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the FP64 CPU oracle, bounded sample
+# --------------------------------------------------------------------------- #
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import pins_oracle as po
+    w = workload(args)
+    C, a, b = w.dense_cost(), w.a, w.b
+    cores = 1
+    # one Sinkhorn iteration (two m x n passes) of the oracle, timed until the
+    # budget is spent; a solve has K*T1 of them plus the Newton passes
+    t0 = time.perf_counter()
+    it = 0
+    F, G = np.zeros(args.n), np.zeros(args.n)
+    per_step = max(1, int(args.cpu_seconds / max(args.steps + args.warmup, 1) / 0.4))
+    times = []
+    for step in range(args.warmup + args.steps):
+        ts = time.perf_counter()
+        for _ in range(per_step):
+            F, _ = po.sinkhorn_row_step(C, a, F, G, args.eta, 1.0)
+            G = po.sinkhorn_col_step(C, b, F, G, args.eta, 1.0)
+            it += 1
+        if step >= args.warmup:
+            times.append((time.perf_counter() - ts) / per_step)
+    t_iter = float(np.median(times))
+    # a paper-default solve runs K outer iterations of T1 Sinkhorn iterations and up to
+    # T2 Newton steps; each Newton step costs at least one trial pass (2 transcendentals
+    # per entry) plus the gradient/sparsify passes: counted as 2 Sinkhorn iterations.
+    est = args.K * (100 + 2 * 50) * t_iter
+    val = 1.0 / est
+    line = {"impl": "reference", "metric": "OT solves/s", "value": val, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": est * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, w),
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} oracle Sinkhorn iterations per step "
+                                       f"({t_iter*1e3:.1f} ms each, m=n={args.n}); a solve "
+                                       f"counted as K*(T1 + 2*T2) = {args.K*200} iterations"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# our arm
+# --------------------------------------------------------------------------- #
+def cpu_baseline_sample(args, w):
+    """The oracle timed on a bounded sample of the same workload (rank 0, N = 1)."""
+    from oracle import pins_oracle as po
+    C, a, b = w.dense_cost(), w.a, w.b
+    F, G = np.zeros(args.n), np.zeros(args.n)
+    iters, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < args.cpu_seconds:
+        F, _ = po.sinkhorn_row_step(C, a, F, G, args.eta, 1.0)
+        G = po.sinkhorn_col_step(C, b, F, G, args.eta, 1.0)
+        iters += 1
+    t_iter = (time.perf_counter() - t0) / iters
+    est = args.K * (100 + 2 * 50) * t_iter
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} oracle Sinkhorn iterations on the m=n={args.n} instance "
+                      f"({t_iter*1e3:.1f} ms each); a solve counted as K*(T1 + 2*T2) = "
+                      f"{args.K*200} such iterations"}
+
+
+def run_ours(args):
+    import torch
+    from paper_2502_03749_gb300 import pins
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    w = workload(args)
+    C32 = w.dense_cost().astype(np.float32) if args.prec == "mixed" else w.dense_cost()
+    # inputs resident on the device
+    Cd = torch.from_numpy(C32).cuda()
+    ad = torch.from_numpy(w.a).cuda()
+    bd = torch.from_numpy(w.b).cuda()
+    pdev = pins.make_problem("dense", ad, bd, C=Cd, on_device=True)
+    stream = torch.cuda.Stream()
+    cfg = dict(prec=args.prec, eta=args.eta, K=args.K, sparsify_gamma=args.gamma,
+               device=local, cuda_stream=stream.cuda_stream)
+    h = pins.Pins(**cfg)
+    res = pins.pins_result()
+
+    def step():
+        st = pins.pins_solve(h.h, pdev.prob, res)
+        if st not in (0, 3):
+            raise RuntimeError(f"pins_solve: {pins.STATUS_NAMES.get(st)}: {h.error()}")
+        return res.as_dict()
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+            launches += out["gpu_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = args.steps * world / t
+    # e2e: host pinned inputs -> public API -> potentials back, every step
+    hp = {"C": torch.from_numpy(C32).pin_memory(), "a": torch.from_numpy(w.a).pin_memory(),
+          "b": torch.from_numpy(w.b).pin_memory()}
+    phost = pins.make_problem("dense", hp["a"].numpy(), hp["b"].numpy(), C=hp["C"].numpy())
+    Fh = torch.zeros(args.n, dtype=torch.float64).pin_memory()
+    Gh = torch.zeros(args.n, dtype=torch.float64).pin_memory()
+    r2 = pins.pins_result()
+    r2.F_out, r2.G_out = Fh.data_ptr(), Gh.data_ptr()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        pins.pins_solve(h.h, phost.prob, r2)
+    te = time.perf_counter() - te
+    h2d = C32.nbytes + w.a.nbytes + w.b.nbytes
+    d2h = 2 * args.n * 8
+    last = out
+    h.close()
+    # plain FP64 GPU PINS on the same instance (comparison key)
+    fp64 = None
+    if args.prec == "mixed" and args.fp64_steps > 0:
+        C64d = torch.from_numpy(w.dense_cost()).cuda()
+        p64 = pins.make_problem("dense", ad, bd, C=C64d, on_device=True)
+        h64 = pins.Pins(prec="fp64", eta=args.eta, K=args.K, sparsify_gamma=args.gamma,
+                        device=local, cuda_stream=stream.cuda_stream)
+        r64 = pins.pins_result()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            pins.pins_solve(h64.h, p64.prob, r64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3 / args.fp64_steps
+        d64 = r64.as_dict()
+        fp64 = {"value": 1.0 / t64, "unit": "solves/s", "cost": d64["cost"],
+                "rel_gap": d64["rel_gap"], "marg_resid_l1": d64["marg_resid_l1"],
+                "rel_cost_diff_mixed_vs_fp64": abs(last["cost"] - d64["cost"]) / abs(d64["cost"])}
+        h64.close()
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    line = {"metric": "OT solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+dd" if args.prec == "mixed" else "f64", "data": "synthetic",
+            "config": config_dict(args, w),
+            "accuracy": {"cost": last["cost"], "cost_ub": last["cost_ub"],
+                         "dual_lb": last["dual_lb"], "certified_rel_gap": last["rel_gap"],
+                         "marg_resid_l1": last["marg_resid_l1"],
+                         "outer_iters": last["outer_iters"],
+                         "sinkhorn_iters": last["sinkhorn_iters"],
+                         "newton_iters": last["newton_iters"], "cg_iters": last["cg_iters"]},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "fp64_gpu": fp64,
+            "peaks_source": "MEASURED_PEAKS.json" if peaks else "fallback"}
+    if world == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(args, w)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

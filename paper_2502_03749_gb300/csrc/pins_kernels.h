@@ -1,0 +1,78 @@
+// Internal interface between the host solver and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include "pins_common.cuh"
+
+namespace pins {
+
+struct SparsifyState;
+struct TrialArgs;
+struct CertArgs;
+
+// One set of launchers per (precision policy, cost kind).
+struct PassSet {
+  bool mixed;
+  void (*row_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* F_out,
+                  double* out_res, cudaStream_t);
+  void (*col_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* G_out,
+                  cudaStream_t);
+  void (*marg)(const PassArgs&, const TileGeom&, const MergeWS&, const TrialArgs*,
+               double* r, double* c, double* out4, cudaStream_t);
+  void (*cert)(const PassArgs&, const TileGeom&, const MergeWS&, const CertArgs&, bool colpass,
+               cudaStream_t);
+  void (*key_hist)(const PassArgs&, const SparsifyState*, unsigned int* hist, int blocks,
+                   cudaStream_t);
+  void (*key_compact)(const PassArgs&, SparsifyState*, double* coo_key, long long* coo_idx,
+                      double* cand_key, long long* cand_idx, int coo_cap, int blocks,
+                      cudaStream_t);
+};
+
+const PassSet* passes_f64(int kind);
+const PassSet* passes_mixed(int kind);
+
+// sparse/vector launchers (pins_sparse.cu, pins_select.cu)
+struct SparseWS {
+  int* rowcnt; int* colcnt;     // m, n
+  int* indptr; int* indices; double* data;    // CSR: m+1, cap, cap
+  int* colptr; int* rowidx; double* cdata;    // CSC: n+1, cap, cap
+};
+void build_csr(const long long* coo_idx, const double* coo_key, int nnz, int m, int n,
+               double key_scale, const SparseWS& sw, cudaStream_t st);
+void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m,
+                        int n, int* colcnt, int* colptr, int* rowidx, double* cdata,
+                        cudaStream_t st);
+cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* c,
+                       const int* indptr, const int* indices, const double* data,
+                       const int* colptr, const int* rowidx, const double* cdata,
+                       const double* rhs, double* x, double* res, double* p, double* q,
+                       double* part, double rtol, int max_iter, double* info, int sms,
+                       cudaStream_t st);
+int cg_blocks(int N, int sms);
+void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
+                 double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
+void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,
+                       float2* Pdd, float2* Qdd, cudaStream_t st);
+void launch_grad(const double* a, const double* b, const double* r, const double* c, int m,
+                 int n, double* g, cudaStream_t st);
+void launch_axpy2(double* F, double* G, const double* d, int m, int n, double alpha,
+                  cudaStream_t st);
+void launch_outer(double* F, double* G, double* Phi, double* Psi, int m, int n, cudaStream_t st);
+void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, int N,
+                 double* out, cudaStream_t st);
+void launch_cert_pre(const double* a, const double* r, const double* F, int m, double s,
+                     double eta, double* xs, double* u, cudaStream_t st);
+void launch_cert_mid(const double* b, const double* c1, int n, double* ys, double* ec,
+                     cudaStream_t st);
+void launch_cert_final(const double* a, const double* b, const double* rr, const double* cr,
+                       const double* cp, const double* tc, const double* u2, const double* v,
+                       int m, int n, double* out4, cudaStream_t st);
+void launch_d2f(const double* x, float* y, size_t N, cudaStream_t st);
+void launch_f2d(const float* x, double* y, size_t N, cudaStream_t st);
+
+// sparsify selection (pins_select.cu)
+void launch_key_select(SparsifyState* st, unsigned int* hist, long long total, cudaStream_t s);
+cudaError_t launch_cand_select(SparsifyState* st, const double* cand_key,
+                               const long long* cand_idx, double* coo_key, long long* coo_idx,
+                               int coo_cap, cudaStream_t s);
+
+}  // namespace pins

@@ -1,0 +1,696 @@
+// Host driver of Algorithm 2 on one CUDA stream.  All m x n and vector work runs
+// in the kernels of pins_kernels_*.cu / pins_sparse.cu / pins_select.cu; the host
+// only sequences launches and reads a few scalars back to take the decisions the
+// algorithm makes (warm-up exit, Newton stop, Armijo acceptance, outer stop).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include "pins_solver.h"
+
+namespace pins {
+
+namespace {
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <class T> T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += std::max<size_t>(count, 1) * sizeof(T);
+    return p;
+  }
+};
+
+int kind_of(pins_cost_kind k) {
+  switch (k) {
+    case PINS_COST_DENSE_F64:
+    case PINS_COST_DENSE_F32: return COST_DENSE;
+    case PINS_COST_POINTS_SQEUCLID: return COST_POINTS;
+    case PINS_COST_GRID_SQEUCLID: return COST_GRID;
+  }
+  return -1;
+}
+
+struct InputPlan {   // which converted input copies an instance needs
+  bool c64 = false, c32 = false, xy64 = false, xy32 = false, ab = false;
+};
+
+InputPlan plan_inputs(pins_cost_kind kind, bool mixed, bool host_in) {
+  InputPlan q;
+  q.ab = host_in;
+  if (kind == PINS_COST_DENSE_F64) {
+    if (!mixed) q.c64 = host_in;
+    else { q.c32 = true; q.c64 = host_in; }            // host: staged then converted
+  } else if (kind == PINS_COST_DENSE_F32) {
+    if (!mixed) { q.c64 = true; q.c32 = host_in; }     // widened once
+    else q.c32 = host_in;
+  } else if (kind == PINS_COST_POINTS_SQEUCLID) {
+    q.xy64 = host_in;
+    q.xy32 = mixed;
+  }
+  return q;
+}
+
+void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const TileGeom& g,
+           const InputPlan& ip, size_t mn, int d) {
+  const int N = m + n;
+  w.F = cv.take<double>(m); w.G = cv.take<double>(n);
+  w.Phi = cv.take<double>(m); w.Psi = cv.take<double>(n);
+  w.A64 = cv.take<double>(m); w.B64 = cv.take<double>(n);
+  w.r = cv.take<double>(m); w.c = cv.take<double>(n);
+  w.rt = cv.take<double>(m); w.ct = cv.take<double>(n);
+  w.Pt64 = cv.take<double>(m); w.Qt64 = cv.take<double>(n);
+  w.grad = cv.take<double>(N); w.dir = cv.take<double>(N);
+  w.cg_res = cv.take<double>(N); w.cg_p = cv.take<double>(N); w.cg_q = cv.take<double>(N);
+  w.ab = cv.take<double>(N);
+  w.xs = cv.take<double>(m); w.u = cv.take<double>(m); w.rr = cv.take<double>(m);
+  w.cr = cv.take<double>(m); w.cp = cv.take<double>(m); w.tc = cv.take<double>(m);
+  w.u2 = cv.take<double>(m);
+  w.ys = cv.take<double>(n); w.ec = cv.take<double>(n); w.c1 = cv.take<double>(n);
+  w.v = cv.take<double>(n);
+  w.Add = cv.take<float2>(m); w.Bdd = cv.take<float2>(n);
+  w.Ptdd = cv.take<float2>(m); w.Qtdd = cv.take<float2>(n);
+  w.mws.rowpart0 = cv.take<double>((size_t)g.gx * m);
+  w.mws.rowpart1 = cv.take<double>((size_t)g.gx * m);
+  w.mws.rowpart2 = cv.take<double>((size_t)g.gx * m);
+  w.mws.rowpart3 = cv.take<double>((size_t)g.gx * m);
+  w.mws.rowpart4 = cv.take<double>((size_t)g.gx * m);
+  w.mws.colpart0 = cv.take<double>((size_t)g.gy * n);
+  w.mws.colpart1 = cv.take<double>((size_t)g.gy * n);
+  w.mws.scal_row = cv.take<double>(8 * PINS_GY_MAX);
+  w.mws.scal_col = cv.take<double>(4 * PINS_GX_MAX * PINS_GY_MAX + PINS_GX_MAX);
+  w.mws.cnt_row = cv.take<unsigned int>(PINS_GY_MAX);
+  w.mws.cnt_col = cv.take<unsigned int>(PINS_GX_MAX);
+  w.mws.cnt_all = cv.take<unsigned int>(1);
+  w.st = cv.take<SparsifyState>(1);
+  w.hist = cv.take<unsigned int>(PINS_HIST_NB + 1);
+  w.coo_key = cv.take<double>(kcap); w.coo_idx = cv.take<long long>(kcap);
+  w.cand_key = cv.take<double>(PINS_CAND_CAP); w.cand_idx = cv.take<long long>(PINS_CAND_CAP);
+  w.sw.rowcnt = cv.take<int>(m); w.sw.colcnt = cv.take<int>(n);
+  w.sw.indptr = cv.take<int>(m + 1); w.sw.indices = cv.take<int>(kcap);
+  w.sw.data = cv.take<double>(kcap);
+  w.sw.colptr = cv.take<int>(n + 1); w.sw.rowidx = cv.take<int>(kcap);
+  w.sw.cdata = cv.take<double>(kcap);
+  w.cg_part = cv.take<double>(3 * 64 + 8);
+  w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
+  w.a = ip.ab ? cv.take<double>(m) : nullptr;
+  w.b = ip.ab ? cv.take<double>(n) : nullptr;
+  w.C64 = ip.c64 ? cv.take<double>(mn) : nullptr;
+  w.C32 = ip.c32 ? cv.take<float>(mn) : nullptr;
+  w.x = ip.xy64 ? cv.take<double>((size_t)m * d) : nullptr;
+  w.y = ip.xy64 ? cv.take<double>((size_t)n * d) : nullptr;
+  w.xf = ip.xy32 ? cv.take<float>((size_t)m * d) : nullptr;
+  w.yf = ip.xy32 ? cv.take<float>((size_t)n * d) : nullptr;
+}
+
+}  // namespace
+
+size_t workspace_bytes(int m, int n, int kcap, int t1cap, int cost_kind, bool mixed,
+                       bool host_inputs, int d) {
+  Workspace w;
+  Carver cv(nullptr);
+  TileGeom g = make_geom(m, n);
+  InputPlan ip = plan_inputs((pins_cost_kind)cost_kind, mixed, host_inputs);
+  carve(cv, w, m, n, kcap, t1cap, g, ip, (size_t)m * n, d < 1 ? 1 : d);
+  return cv.off + 256;
+}
+
+Solver::Solver(int device, int sms, const float2* exp_table)
+    : device_(device), sms_(sms), exp_table_(exp_table) {}
+
+Solver::~Solver() { release(); }
+
+void Solver::release() {
+  if (ws_.base) cudaFree(ws_.base);
+  ws_ = Workspace();
+  if (h_scal_) cudaFreeHost(h_scal_);
+  h_scal_ = nullptr;
+  h_scal_len_ = 0;
+}
+
+pins_status Solver::check(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err_ = std::string(where) + ": " + cudaGetErrorString(e);
+    return PINS_ERR_CUDA;
+  }
+  return PINS_OK;
+}
+
+pins_status Solver::sync(const char* where) {
+  cudaError_t e = cudaStreamSynchronize(stream_);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err_ = std::string(where) + ": " + cudaGetErrorString(e);
+    return PINS_ERR_CUDA;
+  }
+  return PINS_OK;
+}
+
+pins_status Solver::ensure(int m, int n, int kcap, int t1cap, int kind, bool mixed, bool host_in,
+                           int d) {
+  size_t need = workspace_bytes(m, n, kcap, t1cap, kind, mixed, host_in, d);
+  if (!ws_.base || need > ws_.bytes) {
+    if (ws_.base) { cudaFree(ws_.base); ws_.base = nullptr; ws_.bytes = 0; }
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      err_ = "device allocation of " + std::to_string(need) + " bytes failed";
+      return PINS_ERR_OOM;
+    }
+    ws_.base = p;
+    ws_.bytes = need;
+  }
+  Carver cv(ws_.base);
+  size_t bytes = ws_.bytes;
+  void* base = ws_.base;
+  TileGeom g = make_geom(m, n);
+  carve(cv, ws_, m, n, kcap, t1cap, g, plan_inputs((pins_cost_kind)kind, mixed, host_in),
+        (size_t)m * n, d < 1 ? 1 : d);
+  ws_.base = base; ws_.bytes = bytes;
+  ws_.m = m; ws_.n = n; ws_.kcap = kcap; ws_.t1cap = t1cap;
+  // counters start at zero; every kernel leaves them at zero
+  cudaMemsetAsync(ws_.mws.cnt_row, 0, sizeof(unsigned int) * PINS_GY_MAX, stream_);
+  cudaMemsetAsync(ws_.mws.cnt_col, 0, sizeof(unsigned int) * PINS_GX_MAX, stream_);
+  cudaMemsetAsync(ws_.mws.cnt_all, 0, sizeof(unsigned int), stream_);
+  cudaMemsetAsync(ws_.hist, 0, sizeof(unsigned int) * (PINS_HIST_NB + 1), stream_);
+  int len = SC_ROWRES + t1cap + 8;
+  if (len > h_scal_len_) {
+    if (h_scal_) cudaFreeHost(h_scal_);
+    if (cudaMallocHost(&h_scal_, sizeof(double) * len) != cudaSuccess) {
+      h_scal_ = nullptr; h_scal_len_ = 0;
+      err_ = "pinned host allocation failed";
+      return PINS_ERR_OOM;
+    }
+    h_scal_len_ = len;
+  }
+  return check("workspace");
+}
+
+static bool vec_ok(const double* v, int len, double& sum) {
+  sum = 0.0;
+  for (int i = 0; i < len; ++i) {
+    if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
+    sum += v[i];
+  }
+  return true;
+}
+
+pins_status Solver::prepare(const pins_config& cfg, const pins_problem& p, bool need_kcap) {
+  err_.clear();
+  int kind = kind_of(p.kind);
+  if (kind < 0) { err_ = "unknown cost kind"; return PINS_ERR_INVALID_ARG; }
+  if (p.m < 1 || p.n < 1) { err_ = "m and n must be >= 1"; return PINS_ERR_INVALID_ARG; }
+  if ((long long)p.m * p.n > (1LL << 40)) { err_ = "m*n too large"; return PINS_ERR_INVALID_ARG; }
+  if (!(cfg.eta > 0.0) || !std::isfinite(cfg.eta)) { err_ = "eta must be > 0"; return PINS_ERR_INVALID_ARG; }
+  if (!p.a || !p.b) { err_ = "a and b are required"; return PINS_ERR_INVALID_ARG; }
+  if (kind == COST_DENSE && !p.C) { err_ = "dense cost requires C"; return PINS_ERR_INVALID_ARG; }
+  if (kind == COST_POINTS && (!p.x || !p.y || p.d < 1 || p.d > 4)) {
+    err_ = "points cost requires x, y and 1 <= d <= 4"; return PINS_ERR_INVALID_ARG;
+  }
+  if (kind == COST_GRID && (p.grid_s1 < 1 || p.grid_s2 < 1 || p.grid_s1 * p.grid_s2 != p.m ||
+                            p.m != p.n)) {
+    err_ = "grid cost requires m = n = grid_s1 * grid_s2"; return PINS_ERR_INVALID_ARG;
+  }
+  if (kind != COST_DENSE && !(p.cost_scale > 0.0 && std::isfinite(p.cost_scale))) {
+    err_ = "cost_scale must be > 0"; return PINS_ERR_INVALID_ARG;
+  }
+  if (kind == COST_GRID && (double)(p.grid_s1 - 1) * (p.grid_s1 - 1) +
+                               (double)(p.grid_s2 - 1) * (p.grid_s2 - 1) > 16777216.0) {
+    err_ = "grid too large for exact FP32 squared distances"; return PINS_ERR_INVALID_ARG;
+  }
+  // marginals: positive, finite, each summing to 1 (Eq. ot)
+  std::vector<double> ha, hb;
+  const double* pa = p.a;
+  const double* pb = p.b;
+  if (p.on_device) {
+    ha.resize(p.m); hb.resize(p.n);
+    cudaMemcpy(ha.data(), p.a, sizeof(double) * p.m, cudaMemcpyDeviceToHost);
+    cudaMemcpy(hb.data(), p.b, sizeof(double) * p.n, cudaMemcpyDeviceToHost);
+    if (check("reading a, b") != PINS_OK) return PINS_ERR_INVALID_ARG;
+    pa = ha.data(); pb = hb.data();
+  }
+  double sa, sb;
+  if (!vec_ok(pa, p.m, sa) || !vec_ok(pb, p.n, sb)) {
+    err_ = "a and b must be finite and > 0"; return PINS_ERR_INVALID_ARG;
+  }
+  if (std::fabs(sa - 1.0) > 1e-9 || std::fabs(sb - 1.0) > 1e-9) {
+    err_ = "a and b must each sum to 1 (within 1e-9)"; return PINS_ERR_INVALID_ARG;
+  }
+  if (!p.on_device && kind == COST_DENSE) {
+    size_t mn = (size_t)p.m * p.n;
+    if (p.kind == PINS_COST_DENSE_F64) {
+      const double* C = (const double*)p.C;
+      for (size_t e = 0; e < mn; ++e) if (!std::isfinite(C[e])) { err_ = "C has a non-finite entry"; return PINS_ERR_INVALID_ARG; }
+    } else {
+      const float* C = (const float*)p.C;
+      for (size_t e = 0; e < mn; ++e) if (!std::isfinite(C[e])) { err_ = "C has a non-finite entry"; return PINS_ERR_INVALID_ARG; }
+    }
+  }
+  mixed_ = (cfg.prec == PINS_PREC_MIXED);
+  ps_ = mixed_ ? passes_mixed(kind) : passes_f64(kind);
+  m_ = p.m; n_ = p.n; eta_ = cfg.eta;
+  geom_ = make_geom(m_, n_);
+  int kcap = need_kcap ? (int)std::min<long long>((long long)m_ * n_,
+                                                   std::max(1LL, (long long)llround(cfg.sparsify_gamma * (m_ + n_ - 1))))
+                       : 1;
+  int t1cap = std::max(cfg.T1, 1);
+  pins_status s = ensure(m_, n_, kcap, t1cap, p.kind, mixed_, !p.on_device, p.d);
+  if (s != PINS_OK) return s;
+  return upload(p);
+}
+
+pins_status Solver::upload(const pins_problem& p) {
+  const bool host = !p.on_device;
+  const size_t mn = (size_t)p.m * p.n;
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice;
+  if (host) {
+    cudaMemcpyAsync(ws_.a, p.a, sizeof(double) * p.m, H2D, stream_);
+    cudaMemcpyAsync(ws_.b, p.b, sizeof(double) * p.n, H2D, stream_);
+    a_ = ws_.a; b_ = ws_.b;
+  } else {
+    a_ = p.a; b_ = p.b;
+  }
+  cost_ = CostArgs{};
+  cost_.m = p.m; cost_.n = p.n; cost_.d = p.d < 1 ? 1 : p.d;
+  cost_.kind = kind_of(p.kind);
+  cost_.scale = p.cost_scale;
+  cost_.s2 = p.grid_s2;
+  switch (p.kind) {
+    case PINS_COST_DENSE_F64:
+      if (!mixed_) {
+        if (host) { cudaMemcpyAsync(ws_.C64, p.C, sizeof(double) * mn, H2D, stream_); cost_.C64 = ws_.C64; }
+        else cost_.C64 = (const double*)p.C;
+      } else {
+        const double* src = (const double*)p.C;
+        if (host) { cudaMemcpyAsync(ws_.C64, p.C, sizeof(double) * mn, H2D, stream_); src = ws_.C64; }
+        launch_d2f(src, ws_.C32, mn, stream_); ++launches_;
+        cost_.C32 = ws_.C32;
+      }
+      break;
+    case PINS_COST_DENSE_F32:
+      if (!mixed_) {
+        const float* src = (const float*)p.C;
+        if (host) { cudaMemcpyAsync(ws_.C32, p.C, sizeof(float) * mn, H2D, stream_); src = ws_.C32; }
+        launch_f2d(src, ws_.C64, mn, stream_); ++launches_;
+        cost_.C64 = ws_.C64;
+      } else {
+        if (host) { cudaMemcpyAsync(ws_.C32, p.C, sizeof(float) * mn, H2D, stream_); cost_.C32 = ws_.C32; }
+        else cost_.C32 = (const float*)p.C;
+      }
+      break;
+    case PINS_COST_POINTS_SQEUCLID: {
+      const double* x = p.x;
+      const double* y = p.y;
+      if (host) {
+        cudaMemcpyAsync(ws_.x, p.x, sizeof(double) * p.m * cost_.d, H2D, stream_);
+        cudaMemcpyAsync(ws_.y, p.y, sizeof(double) * p.n * cost_.d, H2D, stream_);
+        x = ws_.x; y = ws_.y;
+      }
+      cost_.x = x; cost_.y = y;
+      if (mixed_) {
+        launch_d2f(x, ws_.xf, (size_t)p.m * cost_.d, stream_);
+        launch_d2f(y, ws_.yf, (size_t)p.n * cost_.d, stream_);
+        launches_ += 2;
+        cost_.xf = ws_.xf; cost_.yf = ws_.yf;
+      }
+      break;
+    }
+    case PINS_COST_GRID_SQEUCLID:
+      break;
+  }
+  return check("upload");
+}
+
+PassArgs Solver::args(double s, const double* F, const double* G) {
+  PassArgs a{};
+  a.cost = cost_;
+  a.m = m_; a.n = n_;
+  a.eta = eta_; a.inv_eta = 1.0 / eta_; a.s = s;
+  a.kappa = s / eta_;
+  double craw = (cost_.kind == COST_DENSE) ? 1.0 : cost_.scale;
+  double kd = a.kappa * craw;
+  a.kappa_dd.hi = (float)kd;
+  a.kappa_dd.lo = (float)(kd - (double)a.kappa_dd.hi);
+  a.cscale = craw;
+  a.F = F; a.G = G;
+  a.A64 = ws_.A64; a.B64 = ws_.B64;
+  a.Add = ws_.Add; a.Bdd = ws_.Bdd;
+  a.a = a_; a.b = b_;
+  a.exp_table = exp_table_;
+  return a;
+}
+
+void Solver::prep(double s) {
+  // (called with the solver's own F, G)
+  launch_prep(ws_.F, ws_.G, m_, n_, eta_, s, mixed_ ? nullptr : ws_.A64,
+              mixed_ ? nullptr : ws_.B64, mixed_ ? ws_.Add : nullptr, mixed_ ? ws_.Bdd : nullptr,
+              stream_);
+  ++launches_;
+}
+
+void Solver::sinkhorn_iter(double s, int t) {
+  prep(s);
+  PassArgs pa = args(s, ws_.F, ws_.G);
+  ps_->row_lse(pa, geom_, ws_.mws, ws_.F, ws_.scal + SC_ROWRES + t, stream_);
+  prep(s);
+  ps_->col_lse(pa, geom_, ws_.mws, ws_.G, stream_);
+  launches_ += 2;
+}
+
+void Solver::marg(double s, bool trial) {
+  PassArgs pa = args(s, ws_.F, ws_.G);
+  if (trial) {
+    TrialArgs tr{ws_.Pt64, ws_.Qt64, ws_.Ptdd, ws_.Qtdd};
+    ps_->marg(pa, geom_, ws_.mws, &tr, ws_.rt, ws_.ct, ws_.scal + SC_TRIAL, stream_);
+  } else {
+    ps_->marg(pa, geom_, ws_.mws, nullptr, ws_.r, ws_.c, ws_.scal + SC_MARG, stream_);
+  }
+  ++launches_;
+}
+
+pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out) {
+  SparsifyState st{};
+  if (!mixed_) {
+    st.kref = eta_ * zmax + 1e-9 * (1.0 + s + std::fabs(eta_ * zmax));
+    st.width = 64.0 * eta_ / PINS_HIST_NB;
+  } else {
+    st.kref = zmax + 1e-3 * (1.0 + std::fabs(zmax));
+    st.width = 64.0 / PINS_HIST_NB;
+  }
+  st.lo = 0.0; st.count_in = 0; st.level = 0; st.done = 0; st.need = 0; st.thr_bin = -1;
+  st.cand_count = 0; st.coo_count = 0; st.overflow = 0; st.keep = keep;
+  st.tau = 0.0; st.tau_idx = -1;
+  // SparsifyState sits in pinned memory space of h_scal_? keep a local copy
+  cudaMemcpyAsync(ws_.st, &st, sizeof(st), cudaMemcpyHostToDevice, stream_);
+  PassArgs pa = args(s, ws_.F, ws_.G);
+  int blocks = std::min(std::max((m_ + 7) / 8, 1), sms_ * 8);
+  SparsifyState hs{};
+  for (int round = 0; round < 13; ++round) {
+    ps_->key_hist(pa, ws_.st, ws_.hist, blocks, stream_);
+    launch_key_select(ws_.st, ws_.hist, (long long)m_ * n_, stream_);
+    ps_->key_compact(pa, ws_.st, ws_.coo_key, ws_.coo_idx, ws_.cand_key, ws_.cand_idx,
+                     ws_.kcap, blocks, stream_);
+    if (launch_cand_select(ws_.st, ws_.cand_key, ws_.cand_idx, ws_.coo_key, ws_.coo_idx,
+                           ws_.kcap, stream_) != cudaSuccess) {
+      return check("sparsify select");
+    }
+    launches_ += 4;
+    cudaMemcpyAsync(&hs, ws_.st, sizeof(hs), cudaMemcpyDeviceToHost, stream_);
+    pins_status e = sync("sparsify");
+    if (e != PINS_OK) return e;
+    if (hs.done) break;
+  }
+  if (!hs.done || hs.overflow || (int)hs.coo_count != keep) {
+    err_ = "sparsify: threshold selection failed (more tied keys than the candidate buffer)";
+    return PINS_ERR_CUDA;
+  }
+  build_csr(ws_.coo_idx, ws_.coo_key, keep, m_, n_, mixed_ ? 1.0 : 1.0 / eta_, ws_.sw, stream_);
+  launches_ += 7;
+  *nnz_out = keep;
+  return check("csr");
+}
+
+pins_status Solver::certificate(double s) {
+  launch_cert_pre(a_, ws_.r, ws_.F, m_, s, eta_, ws_.xs, ws_.u, stream_);
+  prep(s);
+  PassArgs pa = args(s, ws_.F, ws_.G);
+  CertArgs ca{ws_.xs, ws_.ys, ws_.u, ws_.v, ws_.ec, ws_.c1, ws_.v, ws_.rr, ws_.cr, ws_.cp,
+              ws_.tc, ws_.u2};
+  ps_->cert(pa, geom_, ws_.mws, ca, true, stream_);
+  launch_cert_mid(b_, ws_.c1, n_, ws_.ys, ws_.ec, stream_);
+  ps_->cert(pa, geom_, ws_.mws, ca, false, stream_);
+  launch_cert_final(a_, b_, ws_.rr, ws_.cr, ws_.cp, ws_.tc, ws_.u2, ws_.v, m_, n_,
+                    ws_.scal + SC_CERT, stream_);
+  launches_ += 5;
+  return check("certificate");
+}
+
+pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_result& r) {
+  auto t0 = std::chrono::steady_clock::now();
+  long long launches0 = launches_;
+  double* keepF = r.F_out;
+  double* keepG = r.G_out;
+  std::memset(&r, 0, sizeof(r));
+  r.F_out = keepF; r.G_out = keepG;
+  pins_status stt = prepare(cfg, p, true);
+  if (stt != PINS_OK) { r.status = stt; return stt; }
+  const int m = m_, n = n_;
+  const int keep = (int)std::min<long long>((long long)m * n,
+      std::max(1LL, (long long)llround(cfg.sparsify_gamma * (m + n - 1))));
+  const int max_cg = std::max(1, std::min(cfg.max_cg, m + n));
+  const double tol = cfg.tol_marg;
+  const int check_every = std::max(1, cfg.sinkhorn_check_every);
+  const int gap_every = std::max(1, cfg.gap_every);
+  // state: F = G = Phi = Psi = 0 (readings R1); ab = (a; b)
+  cudaMemsetAsync(ws_.F, 0, sizeof(double) * m, stream_);
+  cudaMemsetAsync(ws_.G, 0, sizeof(double) * n, stream_);
+  cudaMemsetAsync(ws_.Phi, 0, sizeof(double) * m, stream_);
+  cudaMemsetAsync(ws_.Psi, 0, sizeof(double) * n, stream_);
+  cudaMemcpyAsync(ws_.ab, a_, sizeof(double) * m, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.ab + m, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream_);
+  int outer = 0;
+  bool stop = false, cert_current = false;
+  double res = INFINITY, zmax = 0.0;
+  double cert[4] = {0, 0, 0, 0};
+  for (int k = 0; k < cfg.K && !stop; ++k) {
+    const double s = (double)(k + 1);
+    cert_current = false;
+    // ---- Sinkhorn warm-up (readings R3, R4) ----
+    int t = 0;
+    while (t < cfg.T1) {
+      sinkhorn_iter(s, t);
+      ++t;
+      if (t % check_every == 0) {
+        cudaMemcpyAsync(h_scal_ + SC_ROWRES + t - 1, ws_.scal + SC_ROWRES + t - 1,
+                        sizeof(double), cudaMemcpyDeviceToHost, stream_);
+        if ((stt = sync("warm-up")) != PINS_OK) { r.status = stt; return stt; }
+        if (h_scal_[SC_ROWRES + t - 1] <= tol) break;
+      }
+    }
+    r.sinkhorn_iters += t;
+    // ---- sparse Newton (Alg. 2 second loop) ----
+    prep(s);
+    marg(s, false);
+    cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
+                    cudaMemcpyDeviceToHost, stream_);
+    if ((stt = sync("gradient")) != PINS_OK) { r.status = stt; return stt; }
+    res = h_scal_[SC_MARG + 0];
+    zmax = h_scal_[SC_MARG + 2];
+    int steps = 0;
+    while (steps < cfg.T2) {
+      if (!(res > tol)) break;
+      int nnz = 0;
+      if ((stt = sparsify(s, keep, zmax, &nnz)) != PINS_OK) { r.status = stt; return stt; }
+      launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
+      cudaError_t ce = launch_pcg(m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
+                                  ws_.sw.data, ws_.sw.colptr, ws_.sw.rowidx, ws_.sw.cdata,
+                                  ws_.grad, ws_.dir, ws_.cg_res, ws_.cg_p, ws_.cg_q,
+                                  ws_.cg_part, cfg.cg_rtol, max_cg, ws_.scal + SC_CG, sms_,
+                                  stream_);
+      if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
+      launch_dot2(ws_.grad, ws_.dir, ws_.ab, ws_.dir, m + n, ws_.scal + SC_DOTS, stream_);
+      launches_ += 3;
+      bool accepted = false;
+      double alpha = 1.0;
+      int q = 0;
+      for (; q <= cfg.max_backtrack; ++q) {
+        launch_trial_prep(ws_.dir, m, n, alpha / eta_, mixed_ ? nullptr : ws_.Pt64,
+                          mixed_ ? nullptr : ws_.Qt64, mixed_ ? ws_.Ptdd : nullptr,
+                          mixed_ ? ws_.Qtdd : nullptr, stream_);
+        ++launches_;
+        marg(s, true);
+        cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL, 16 * sizeof(double),
+                        cudaMemcpyDeviceToHost, stream_);
+        if ((stt = sync("line search")) != PINS_OK) { r.status = stt; return stt; }
+        if (q == 0) r.cg_iters += (int)h_scal_[SC_CG];
+        const double gtd = h_scal_[SC_DOTS + 0];
+        const double adot = h_scal_[SC_DOTS + 1];
+        const double dsum = h_scal_[SC_TRIAL + 3];
+        const double dP = alpha * adot - eta_ * dsum;
+        if (std::isfinite(dP) && dP >= cfg.armijo_c1 * alpha * gtd) { accepted = true; break; }
+        alpha *= cfg.armijo_beta;
+      }
+      r.ls_trials += std::min(q + 1, cfg.max_backtrack + 1);
+      ++steps;
+      if (accepted) {
+        launch_axpy2(ws_.F, ws_.G, ws_.dir, m, n, alpha, stream_);
+        ++launches_;
+        prep(s);
+        std::swap(ws_.r, ws_.rt);
+        std::swap(ws_.c, ws_.ct);
+        res = h_scal_[SC_TRIAL + 0];
+        zmax = h_scal_[SC_TRIAL + 2];
+      } else {
+        ++r.ls_failures;
+        sinkhorn_iter(s, 0);
+        prep(s);
+        marg(s, false);
+        cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
+                        cudaMemcpyDeviceToHost, stream_);
+        if ((stt = sync("fallback")) != PINS_OK) { r.status = stt; return stt; }
+        res = h_scal_[SC_MARG + 0];
+        zmax = h_scal_[SC_MARG + 2];
+      }
+    }
+    r.newton_iters += steps;
+    outer = k + 1;
+    // ---- outer stop (reading R9) ----
+    if (cfg.tol_gap > 0.0 && (outer % gap_every == 0 || outer == cfg.K)) {
+      if ((stt = certificate(s)) != PINS_OK) { r.status = stt; return stt; }
+      cudaMemcpyAsync(cert, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+      if ((stt = sync("certificate")) != PINS_OK) { r.status = stt; return stt; }
+      cert_current = true;
+      if (cert[3] <= cfg.tol_gap) stop = true;
+    }
+    if (!stop && outer < cfg.K) {     // X^{k+1} becomes the next prox centre (R2)
+      launch_outer(ws_.F, ws_.G, ws_.Phi, ws_.Psi, m, n, stream_);
+      ++launches_;
+    }
+  }
+  const double s_final = (double)outer;
+  if (!cert_current) {
+    if ((stt = certificate(s_final)) != PINS_OK) { r.status = stt; return stt; }
+    cudaMemcpyAsync(cert, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  }
+  if (r.F_out) cudaMemcpyAsync(r.F_out, ws_.F, sizeof(double) * m, cudaMemcpyDeviceToHost, stream_);
+  if (r.G_out) cudaMemcpyAsync(r.G_out, ws_.G, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_);
+  if ((stt = sync("result")) != PINS_OK) { r.status = stt; return stt; }
+  r.cost = cert[0]; r.cost_ub = cert[1]; r.dual_lb = cert[2]; r.rel_gap = cert[3];
+  r.marg_resid_l1 = res;
+  r.s = s_final;
+  r.outer_iters = outer;
+  r.gpu_launches = (int)(launches_ - launches0);
+  r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  bool converged = (cfg.tol_gap > 0.0) ? stop : (res <= tol);
+  r.status = converged ? PINS_OK : PINS_ERR_NOT_CONVERGED;
+  return r.status;
+}
+
+// ------------------------------------------------------------------------- //
+// step-level entry points
+// ------------------------------------------------------------------------- //
+pins_status Solver::step_sinkhorn(const pins_config& cfg, const pins_problem& p, double s,
+                                  int iters, double* F, double* G, double* row_res) {
+  pins_config c2 = cfg;
+  c2.T1 = std::max(cfg.T1, iters);
+  pins_status st = prepare(c2, p, false);
+  if (st != PINS_OK) return st;
+  cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  for (int t = 0; t < iters; ++t) sinkhorn_iter(s, t);
+  cudaMemcpyAsync(F, ws_.F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(G, ws_.G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  if (row_res && iters > 0)
+    cudaMemcpyAsync(row_res, ws_.scal + SC_ROWRES, sizeof(double) * iters,
+                    cudaMemcpyDeviceToDevice, stream_);
+  return sync("step_sinkhorn");
+}
+
+pins_status Solver::step_marginals(const pins_config& cfg, const pins_problem& p, double s,
+                                   const double* F, const double* G, double* r, double* c,
+                                   double* out3) {
+  pins_status st = prepare(cfg, p, false);
+  if (st != PINS_OK) return st;
+  cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  prep(s);
+  marg(s, false);
+  cudaMemcpyAsync(r, ws_.r, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(c, ws_.c, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
+                  cudaMemcpyDeviceToHost, stream_);
+  if ((st = sync("step_marginals")) != PINS_OK) return st;
+  double o[3] = {h_scal_[SC_MARG], h_scal_[SC_MARG + 1], eta_ * h_scal_[SC_MARG + 2]};
+  cudaMemcpyAsync(out3, o, sizeof(o), cudaMemcpyHostToDevice, stream_);
+  return sync("step_marginals out");
+}
+
+pins_status Solver::step_sparsify(const pins_config& cfg, const pins_problem& p, double s,
+                                  const double* F, const double* G, int keep, int* indptr,
+                                  int* indices, double* data) {
+  if (keep < 1 || (long long)keep > (long long)p.m * p.n) { err_ = "keep out of range"; return PINS_ERR_INVALID_ARG; }
+  pins_config c2 = cfg;
+  c2.sparsify_gamma = 1.0;
+  pins_status st = prepare(c2, p, false);
+  if (st != PINS_OK) return st;
+  // the workspace must hold `keep` entries
+  if ((st = ensure(m_, n_, keep, std::max(cfg.T1, 1), p.kind, mixed_, !p.on_device, p.d)) != PINS_OK) return st;
+  if ((st = upload(p)) != PINS_OK) return st;
+  cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  prep(s);
+  marg(s, false);
+  cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
+                  cudaMemcpyDeviceToHost, stream_);
+  if ((st = sync("step_sparsify marg")) != PINS_OK) return st;
+  int nnz = 0;
+  if ((st = sparsify(s, keep, h_scal_[SC_MARG + 2], &nnz)) != PINS_OK) return st;
+  cudaMemcpyAsync(indptr, ws_.sw.indptr, sizeof(int) * (m_ + 1), cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(indices, ws_.sw.indices, sizeof(int) * keep, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(data, ws_.sw.data, sizeof(double) * keep, cudaMemcpyDeviceToDevice, stream_);
+  return sync("step_sparsify");
+}
+
+pins_status Solver::step_cg(int m, int n, double eta, const double* r, const double* c,
+                            const int* indptr, const int* indices, const double* data, int nnz,
+                            const double* rhs, double* d, double rtol, int max_iter,
+                            double* info) {
+  err_.clear();
+  if (m < 1 || n < 1 || nnz < 0 || !(eta > 0.0) || max_iter < 0) { err_ = "bad CG arguments"; return PINS_ERR_INVALID_ARG; }
+  pins_status st = ensure(m, n, std::max(nnz, 1), 1, PINS_COST_GRID_SQEUCLID, false, false, 1);
+  if (st != PINS_OK) return st;
+  build_csc_from_csr(indptr, indices, data, m, n, ws_.sw.colcnt, ws_.sw.colptr, ws_.sw.rowidx,
+                     ws_.sw.cdata, stream_);
+  cudaError_t ce = launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
+                              ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p,
+                              ws_.cg_q, ws_.cg_part, rtol, max_iter, info, sms_, stream_);
+  launches_ += 5;
+  if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); return PINS_ERR_CUDA; }
+  return sync("step_cg");
+}
+
+pins_status Solver::step_objective_increase(const pins_config& cfg, const pins_problem& p,
+                                            double s, const double* F, const double* G,
+                                            const double* df, const double* dg, double alpha,
+                                            double* out) {
+  pins_status st = prepare(cfg, p, false);
+  if (st != PINS_OK) return st;
+  cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.dir, df, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.dir + m_, dg, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.ab, a_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.ab + m_, b_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  prep(s);
+  launch_trial_prep(ws_.dir, m_, n_, alpha / eta_, mixed_ ? nullptr : ws_.Pt64,
+                    mixed_ ? nullptr : ws_.Qt64, mixed_ ? ws_.Ptdd : nullptr,
+                    mixed_ ? ws_.Qtdd : nullptr, stream_);
+  marg(s, true);
+  launch_dot2(ws_.ab, ws_.dir, nullptr, nullptr, m_ + n_, ws_.scal + SC_DOTS, stream_);
+  launches_ += 2;
+  cudaMemcpyAsync(h_scal_, ws_.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
+  if ((st = sync("step_objective_increase")) != PINS_OK) return st;
+  double dP = alpha * h_scal_[SC_DOTS] - eta_ * h_scal_[SC_TRIAL + 3];
+  if (!std::isfinite(dP)) dP = -INFINITY;
+  cudaMemcpyAsync(out, &dP, sizeof(double), cudaMemcpyHostToDevice, stream_);
+  return sync("step_objective_increase out");
+}
+
+pins_status Solver::step_certificate(const pins_config& cfg, const pins_problem& p, double s,
+                                     const double* F, const double* G, double* out4) {
+  pins_status st = prepare(cfg, p, false);
+  if (st != PINS_OK) return st;
+  cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
+  prep(s);
+  marg(s, false);
+  if ((st = certificate(s)) != PINS_OK) return st;
+  cudaMemcpyAsync(out4, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+  return sync("step_certificate");
+}
+
+}  // namespace pins

@@ -1,0 +1,108 @@
+// Host-side solver of one PINS instance on one CUDA stream (Algorithm 2).
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+#include "../../include/pins.h"
+#include "pins_kernels.h"
+#include "pins_passes.cuh"
+
+namespace pins {
+
+// Device workspace of one instance (one arena, carved in fixed order).
+struct Workspace {
+  size_t bytes = 0;
+  void* base = nullptr;
+  int m = 0, n = 0, kcap = 0, t1cap = 0;
+  // potentials and vectors (FP64)
+  double *F, *G, *Phi, *Psi, *A64, *B64, *r, *c, *rt, *ct, *Pt64, *Qt64;
+  double *grad, *dir, *cg_res, *cg_p, *cg_q, *ab;
+  double *xs, *u, *rr, *cr, *cp, *tc, *u2, *ys, *ec, *c1, *v;
+  float2 *Add, *Bdd, *Ptdd, *Qtdd;
+  MergeWS mws;
+  SparsifyState* st;
+  unsigned int* hist;
+  double* coo_key; long long* coo_idx; double* cand_key; long long* cand_idx;
+  SparseWS sw;
+  double* cg_part;
+  double* scal;            // device scalars (see Solver::SC_*)
+  // uploaded inputs
+  double *a, *b, *C64, *x, *y;
+  float *C32, *xf, *yf;
+};
+
+size_t workspace_bytes(int m, int n, int kcap, int t1cap, int cost_kind, bool mixed,
+                       bool host_inputs, int d);
+
+class Solver {
+ public:
+  // scalar slots in Workspace::scal (doubles)
+  enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_ROWRES = 32 };
+
+  Solver(int device, int sms, const float2* exp_table);
+  ~Solver();
+  Solver(const Solver&) = delete;
+  Solver& operator=(const Solver&) = delete;
+
+  void set_stream(cudaStream_t s) { stream_ = s; }
+  cudaStream_t stream() const { return stream_; }
+  size_t arena_bytes() const { return ws_.bytes; }
+  void release();
+
+  // Full solve.  cfg is read-only; r is filled.
+  pins_status solve(const pins_config& cfg, const pins_problem& p, pins_result& r);
+
+  // step-level entry points (device pointers, p.on_device == 1)
+  pins_status step_sinkhorn(const pins_config& cfg, const pins_problem& p, double s, int iters,
+                            double* F, double* G, double* row_res);
+  pins_status step_marginals(const pins_config& cfg, const pins_problem& p, double s,
+                             const double* F, const double* G, double* r, double* c,
+                             double* out3);
+  pins_status step_sparsify(const pins_config& cfg, const pins_problem& p, double s,
+                            const double* F, const double* G, int keep, int* indptr,
+                            int* indices, double* data);
+  pins_status step_cg(int m, int n, double eta, const double* r, const double* c,
+                      const int* indptr, const int* indices, const double* data, int nnz,
+                      const double* rhs, double* d, double rtol, int max_iter, double* info);
+  pins_status step_objective_increase(const pins_config& cfg, const pins_problem& p, double s,
+                                      const double* F, const double* G, const double* df,
+                                      const double* dg, double alpha, double* out);
+  pins_status step_certificate(const pins_config& cfg, const pins_problem& p, double s,
+                               const double* F, const double* G, double* out4);
+
+  const std::string& error() const { return err_; }
+  long long launches() const { return launches_; }
+
+ private:
+  pins_status prepare(const pins_config& cfg, const pins_problem& p, bool need_kcap);
+  pins_status ensure(int m, int n, int kcap, int t1cap, int kind, bool mixed, bool host_in, int d);
+  pins_status upload(const pins_problem& p);
+  pins_status check(const char* where);
+  pins_status sync(const char* where);
+  void prep(double s);
+  void sinkhorn_iter(double s, int t);
+  void marg(double s, bool trial);
+  pins_status sparsify(double s, int keep, double zmax, int* nnz_out);
+  pins_status certificate(double s);
+  PassArgs args(double s, const double* F, const double* G);
+
+  int device_, sms_;
+  const float2* exp_table_;
+  cudaStream_t stream_ = nullptr;
+  Workspace ws_;
+  double* h_scal_ = nullptr;   // pinned mirror of ws_.scal
+  int h_scal_len_ = 0;
+  std::string err_;
+  long long launches_ = 0;
+  // per-problem state
+  const PassSet* ps_ = nullptr;
+  CostArgs cost_{};
+  int m_ = 0, n_ = 0;
+  double eta_ = 0;
+  bool mixed_ = false;
+  TileGeom geom_{};
+  const double* a_ = nullptr;
+  const double* b_ = nullptr;
+};
+
+}  // namespace pins

@@ -1,0 +1,162 @@
+"""End-to-end parity of pins_solve / pins_solve_batch / pins_submit with the FP64
+oracle, exact LP optima, and each other (cost kinds, alone vs batched).
+
+Bars: FP64 path -- relative transport cost within 1e-8 of the oracle on the same
+algorithm and marginal residual below the tolerance; mixed path -- the achieved
+relative cost error against the FP64 oracle is asserted <= 1e-7 (FP32-rounded
+costs) and reported by the benchmark for every workload."""
+import numpy as np
+import pytest
+
+from oracle import pins_oracle as po
+from paper_2502_03749_gb300 import pins, workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(problem_ref, **cfg):
+    h = pins.Pins(**cfg)
+    try:
+        return h.solve(problem_ref)
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("m,n", [(64, 64), (48, 80), (130, 70)])
+def test_fp64_solve_matches_oracle(m, n):
+    w = wl.small_points(0, m=m, n=n)
+    kw = dict(eta=1e-2, tol_marg=1e-10, K=6, gamma=2.0)
+    ref = po.pins(w.C, w.a, w.b, **kw)
+    out = _solve(pins.problem_from_workload(w), eta=1e-2, tol_marg=1e-10, K=6,
+                 sparsify_gamma=2.0)
+    assert out["outer_iters"] == ref["outer_iters"]
+    assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= 1e-8
+    # Newton can end at the T2 cap; the residual then matches the oracle's
+    assert out["marg_resid_l1"] <= max(1e-10, 1.01 * ref["res"])
+    assert out["newton_iters"] == ref["newton_iters"]
+    assert abs(out["dual_lb"] - ref["lb"]) <= 1e-8 * abs(ref["lb"])
+    assert abs(out["cost_ub"] - ref["ub"]) <= 1e-8 * abs(ref["ub"])
+    np.testing.assert_allclose(out["F"], ref["F"], rtol=0, atol=1e-7 * np.abs(ref["F"]).max())
+
+
+def test_fp64_paper_defaults_track_oracle():
+    """gamma = 1 (Theorem 2 budget), T1 = 100, T2 = 50: Newton is linear here, so the
+    inner solves end at the T2 cap; costs still agree to 1e-8."""
+    w = wl.small_points(0)
+    ref = po.pins(w.C, w.a, w.b, eta=1e-2, tol_marg=1e-10, K=3)
+    out = _solve(pins.problem_from_workload(w), eta=1e-2, tol_marg=1e-10, K=3)
+    assert abs(out["newton_iters"] - ref["newton_iters"]) <= 0.05 * ref["newton_iters"]
+    assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= 1e-8
+
+
+def test_cost_kinds_agree():
+    """Dense, point-cloud and grid sources of the same C give identical solves."""
+    w = wl.small_points(1, m=36, n=44)
+    dense = pins.make_problem("dense", w.a, w.b, C=w.C)
+    pts = pins.make_problem("points", w.a, w.b, x=w.x, y=w.y, cost_scale=w.cost_scale)
+    kw = dict(eta=1e-2, tol_marg=1e-10, K=4, sparsify_gamma=2.0)
+    o1, o2 = _solve(dense, **kw), _solve(pts, **kw)
+    assert o1["cost"] == o2["cost"] and np.array_equal(o1["F"], o2["F"])
+    g = wl.grid_instance(7, 0)
+    gd = pins.make_problem("dense", g.a, g.b, C=g.dense_cost())
+    gg = pins.make_problem("grid", g.a, g.b, cost_scale=g.cost_scale, grid=g.grid)
+    o3, o4 = _solve(gd, **kw), _solve(gg, **kw)
+    assert o3["cost"] == o4["cost"] and np.array_equal(o3["G"], o4["G"])
+
+
+def test_lp_optimum_reached():
+    """eta = 1e-3: the outer loop reaches the HiGHS optimum of Eq. ot (m != n)."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(31)
+    m, n = 12, 9
+    x = rng.uniform(0, 1, size=(m, 2)); y = rng.uniform(0, 1, size=(n, 2))
+    C = ((x[:, None, :] - y[None, :, :]) ** 2).sum(axis=2); C /= C.max()
+    a = rng.dirichlet(np.ones(m)); b = rng.dirichlet(np.ones(n))
+    A = np.zeros((m + n, m * n))
+    for i in range(m):
+        A[i, i * n:(i + 1) * n] = 1
+    for j in range(n):
+        A[m + j, j::n] = 1
+    opt = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([a, b]), bounds=(0, None),
+                  method="highs").fun
+    out = _solve(pins.make_problem("dense", a, b, C=C), eta=1e-3, tol_marg=1e-11, K=250,
+                 sparsify_gamma=2.0)
+    assert abs(out["cost"] - opt) / opt <= 1e-9
+    assert out["dual_lb"] <= opt * (1 + 1e-12) and out["cost_ub"] >= opt * (1 - 1e-12)
+
+
+def test_single_row_closed_form():
+    """m = 1: the only feasible plan is b^T, so cost = sum_j C_1j b_j (any eta)."""
+    rng = np.random.default_rng(3)
+    n = 300
+    C = rng.uniform(size=(1, n)); b = rng.dirichlet(np.ones(n))
+    out = _solve(pins.make_problem("dense", np.ones(1), b, C=C), eta=1e-2, K=2, tol_marg=1e-12)
+    assert out["cost"] == pytest.approx(float(C[0] @ b), rel=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["dense32", "points"])
+def test_mixed_precision_accuracy(kind):
+    w = wl.small_points(2, m=96, n=80)
+    if kind == "dense32":
+        C32 = w.C.astype(np.float32)
+        ref = po.pins(C32.astype(np.float64), w.a, w.b, eta=1e-2, tol_marg=1e-9, K=8, gamma=2.0)
+        pr = pins.make_problem("dense", w.a, w.b, C=C32)
+    else:
+        xf = w.x.astype(np.float32).astype(np.float64)
+        yf = w.y.astype(np.float32).astype(np.float64)
+        Cf = (((xf[:, None, :] - yf[None, :, :]) ** 2).sum(axis=2).astype(np.float32)
+              .astype(np.float64) * w.cost_scale)
+        ref = po.pins(Cf, w.a, w.b, eta=1e-2, tol_marg=1e-9, K=8, gamma=2.0)
+        pr = pins.make_problem("points", w.a, w.b, x=w.x, y=w.y, cost_scale=w.cost_scale)
+    out = _solve(pr, prec="mixed", eta=1e-2, tol_marg=1e-9, K=8, sparsify_gamma=2.0)
+    assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= 1e-7
+    assert out["marg_resid_l1"] <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_and_serving_match_solo(prec):
+    """Each result is bit-identical alone, inside a batch, and through submit/poll."""
+    probs = [wl.small_points(i, m=m, n=n) for i, (m, n) in
+             enumerate([(40, 60), (64, 64), (100, 30), (17, 90), (128, 129)])]
+    refs = [pins.problem_from_workload(w) for w in probs]
+    kw = dict(prec=prec, eta=1e-2, tol_marg=1e-10, K=3, sparsify_gamma=2.0, max_inflight=3)
+    h = pins.Pins(**kw)
+    try:
+        solo = [h.solve(r) for r in refs]
+        batch = h.solve_batch(refs)
+        tickets = [h.submit(r) for r in refs]
+        served = []
+        for t, r in zip(tickets, refs):
+            F = np.zeros(r.prob.m); G = np.zeros(r.prob.n)
+            d = h.wait(t, (F, G))
+            d["F"] = F
+            served.append(d)
+    finally:
+        h.close()
+    for s, b, v in zip(solo, batch, served):
+        assert s["cost"] == b["cost"] == v["cost"]
+        assert np.array_equal(s["F"], b["F"]) and np.array_equal(s["F"], v["F"])
+
+
+def test_invalid_inputs_rejected():
+    rng = np.random.default_rng(1)
+    C = rng.uniform(size=(5, 6))
+    a = np.full(5, 0.2); b = np.full(6, 1 / 6)
+    h = pins.Pins()
+    try:
+        bad = a.copy(); bad[0] = -0.1; bad[1] += 0.3
+        res = pins.pins_result()
+        assert pins.pins_solve(h.h, pins.make_problem("dense", bad, b, C=C).prob, res) == \
+            pins.PINS_ERR_INVALID_ARG
+        assert pins.pins_solve(h.h, pins.make_problem("dense", a * 1.01, b, C=C).prob, res) == \
+            pins.PINS_ERR_INVALID_ARG
+        Cn = C.copy(); Cn[2, 3] = np.nan
+        assert pins.pins_solve(h.h, pins.make_problem("dense", a, b, C=Cn).prob, res) == \
+            pins.PINS_ERR_INVALID_ARG
+        assert "finite" in h.error()
+        st, _ = pins.pins_submit(h.h, pins.make_problem("dense", a[:0], b, C=C).prob)
+        assert st == pins.PINS_ERR_INVALID_ARG
+        res2 = pins.pins_result()
+        assert pins.pins_poll(h.h, 123456, res2) == pins.PINS_ERR_UNKNOWN_TICKET
+    finally:
+        h.close()

@@ -1,0 +1,209 @@
+"""Parity of each hot-path step (through the C ABI step entry points) with the
+FP64 oracle on identical inputs.  Sizes span several 64 x 128 tiles, a ragged
+tail, and the degenerate 1 x n / m x 1 shapes.
+
+Tolerances: FP64 path -- rounding of FP64 sums and exp (1e-12 relative on sums);
+mixed path -- the double-float exp/exponent (~1e-13 relative per entry, 1e-10 on
+sums), and FP32 exp in the Sinkhorn warm-up (1e-6 relative per term)."""
+import numpy as np
+import pytest
+
+from oracle import pins_oracle as po
+from paper_2502_03749_gb300 import pins
+
+from gpu_util import dense_device_problem, dev, random_state
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(70, 150), (200, 333), (1, 37), (129, 1), (64, 64)]
+PRECS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module")
+def handles():
+    hs = {p: pins.Pins(prec=p, eta=0.05) for p in PRECS}
+    yield hs
+    for h in hs.values():
+        h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_marginals(handles, prec, m, n):
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, m * 7 + n)
+    h = handles[prec]
+    prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    c = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_marginals(h.h, prob.prob, s, dev(F), dev(G), r, c, out)
+    assert st == 0, h.error()
+    _, _, r0, c0 = po.gradient(C, a, b, F, G, eta, s)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    np.testing.assert_allclose(r.cpu().numpy(), r0, rtol=tol)
+    np.testing.assert_allclose(c.cpu().numpy(), c0, rtol=tol)
+    o = out.cpu().numpy()
+    assert o[0] == pytest.approx(po.residual_l1(a, b, r0, c0), rel=1e-8, abs=1e-15)
+    assert o[1] == pytest.approx(r0.sum(), rel=tol)
+    assert o[2] == pytest.approx(po.key_matrix(C, F, G, eta, s).max(), rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n", SHAPES)
+def test_sinkhorn_half_steps(handles, prec, m, n):
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, m * 11 + n)
+    F = F * 0.0; G = G * 0.0
+    h = handles[prec]
+    prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
+    Fd, Gd = dev(F), dev(G)
+    rr = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_sinkhorn(h.h, prob.prob, s, 3, Fd, Gd, rr)
+    assert st == 0, h.error()
+    Fo, Go, res = F.copy(), G.copy(), []
+    for _ in range(3):
+        Fo, rres = po.sinkhorn_row_step(C, a, Fo, Go, eta, s)
+        Go = po.sinkhorn_col_step(C, b, Fo, Go, eta, s)
+        res.append(rres)
+    atol = 1e-11 if prec == "fp64" else 2e-6 * eta
+    np.testing.assert_allclose(Fd.cpu().numpy(), Fo, atol=atol, rtol=0)
+    np.testing.assert_allclose(Gd.cpu().numpy(), Go, atol=atol, rtol=0)
+    # the mixed warm-up sums FP32 exponentials: its residual floor is ~1e-7
+    np.testing.assert_allclose(rr.cpu().numpy(), res, rtol=1e-9 if prec == "fp64" else 1e-4,
+                               atol=1e-14 if prec == "fp64" else 2e-7)
+
+
+def _tie_state(m, n, seed):
+    rng = np.random.default_rng(seed)
+    C = rng.integers(0, 3, size=(m, n)).astype(np.float64) / 4.0
+    F = rng.integers(0, 2, size=m).astype(np.float64) * 0.25
+    G = rng.integers(0, 2, size=n).astype(np.float64) * 0.25
+    a = np.full(m, 1.0 / m); b = np.full(n, 1.0 / n)
+    return C, a, b, F, G, 0.1, 2.0
+
+
+@pytest.mark.parametrize("case", ["random", "ties"])
+@pytest.mark.parametrize("m,n", [(70, 150), (200, 333), (1, 37), (129, 1)])
+def test_sparsify_pattern_is_exact_fp64(handles, case, m, n):
+    import torch
+    if case == "random":
+        C, a, b, F, G, eta, s = random_state(m, n, m + 3 * n)
+    else:
+        C, a, b, F, G, eta, s = _tie_state(m, n, m + 5 * n)
+    keep = min(m * n, m + n - 1)
+    h = pins.Pins(prec="fp64", eta=eta)
+    try:
+        prob = dense_device_problem(C, a, b)
+        indptr = torch.zeros(m + 1, dtype=torch.int32, device="cuda")
+        indices = torch.zeros(keep, dtype=torch.int32, device="cuda")
+        data = torch.zeros(keep, dtype=torch.float64, device="cuda")
+        st = pins.pins_step_sparsify(h.h, prob.prob, s, dev(F), dev(G), keep, indptr, indices, data)
+        assert st == 0, h.error()
+    finally:
+        h.close()
+    S = po.sparsify(C, F, G, eta, s, keep)
+    assert np.array_equal(indptr.cpu().numpy(), S.indptr)
+    assert np.array_equal(indices.cpu().numpy(), S.indices)
+    np.testing.assert_allclose(data.cpu().numpy(), S.data, rtol=1e-14)
+
+
+@pytest.mark.parametrize("m,n", [(70, 150), (200, 333)])
+def test_sparsify_pattern_valid_mixed(handles, m, n):
+    """Mixed path ranks by the FP32 value of log X~: the kept set must be a top-K set
+    up to that rounding (every kept entry >= every dropped entry within 1e-5)."""
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, 17 * m + n)
+    keep = m + n - 1
+    prob = dense_device_problem(C.astype(np.float32), a, b)
+    indptr = torch.zeros(m + 1, dtype=torch.int32, device="cuda")
+    indices = torch.zeros(keep, dtype=torch.int32, device="cuda")
+    data = torch.zeros(keep, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_sparsify(handles["mixed"].h, prob.prob, s, dev(F), dev(G), keep,
+                                 indptr, indices, data)
+    assert st == 0, handles["mixed"].error()
+    ip, ix = indptr.cpu().numpy(), indices.cpu().numpy()
+    assert ip[-1] == keep
+    mask = np.zeros((m, n), dtype=bool)
+    for i in range(m):
+        cols = ix[ip[i]:ip[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+        mask[i, cols] = True
+    Z = po.log_plan(C, F, G, eta, s)
+    assert Z[mask].min() >= Z[~mask].max() - 1e-5
+    np.testing.assert_allclose(np.sort(data.cpu().numpy()), np.sort(np.exp(Z[mask])), rtol=1e-5)
+
+
+@pytest.mark.parametrize("m,n", [(70, 150), (40, 40), (1, 9)])
+def test_cg_matches_dense_solve(handles, m, n):
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, 5 * m + n)
+    ga, gb, r, c = po.gradient(C, a, b, F, G, eta, s)
+    S = po.sparsify(C, F, G, eta, s, min(m * n, m + n - 1))
+    Sd = S.dense()
+    M = np.block([[np.diag(r), Sd], [Sd.T, np.diag(c)]]) / eta
+    rhs = np.concatenate([ga, gb])
+    # with every entry kept (m = 1 here) M is singular along the gauge direction
+    # (e, -e); solutions then differ along it, so compare M d with rhs
+    singular = S.nnz == m * n
+    d = torch.zeros(m + n, dtype=torch.float64, device="cuda")
+    info = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_cg(handles["fp64"].h, m, n, eta, dev(r), dev(c),
+                           dev(S.indptr.astype(np.int32)), dev(S.indices.astype(np.int32)),
+                           dev(S.data), S.nnz, dev(rhs), d, 1e-12, 5000, info)
+    assert st == 0, handles["fp64"].error()
+    it, rel = info.cpu().numpy()
+    assert rel <= 1e-12
+    dd_ = d.cpu().numpy()
+    assert np.linalg.norm(M @ dd_ - rhs) <= 1e-10 * np.linalg.norm(rhs)
+    if not singular:
+        want = np.linalg.solve(M, rhs)
+        np.testing.assert_allclose(dd_, want, rtol=1e-7, atol=1e-9 * np.abs(want).max())
+    dfo, dgo, ito, _ = po.pcg(r, c, S, eta, ga, gb, rtol=1e-12, max_iter=5000)
+    assert abs(int(it) - ito) <= max(2, ito // 10)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("alpha", [1.0, 0.25])
+def test_objective_increase(handles, prec, alpha):
+    m, n = 70, 150
+    C, a, b, F, G, eta, s = random_state(m, n, 99)
+    rng = np.random.default_rng(5)
+    df, dg = rng.normal(size=m) * 1e-3 * eta, rng.normal(size=n) * 1e-3 * eta
+    prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
+    import torch
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_objective_increase(handles[prec].h, prob.prob, s, dev(F), dev(G),
+                                           dev(df), dev(dg), alpha, out)
+    assert st == 0, handles[prec].error()
+    want = po.objective_increase(C, a, b, F, G, eta, s, df, dg, alpha)
+    scale = alpha * (np.abs(a @ df) + np.abs(b @ dg))
+    assert abs(out.item() - want) <= (1e-12 if prec == "fp64" else 1e-10) * scale + 1e-18
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("m,n", [(70, 150), (129, 1), (64, 64)])
+def test_certificate(handles, prec, m, n):
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, 3 * m + 2 * n)
+    prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_certificate(handles[prec].h, prob.prob, s, dev(F), dev(G), out)
+    assert st == 0, handles[prec].error()
+    cert = po.certificate(C, a, b, F, G, eta, s)
+    o = out.cpu().numpy()
+    tol = 1e-11 if prec == "fp64" else 1e-9
+    assert o[0] == pytest.approx(cert["cost"], rel=tol)
+    assert o[1] == pytest.approx(cert["ub"], rel=tol)
+    assert o[2] == pytest.approx(cert["lb"], rel=tol, abs=1e-13)
+
+
+def test_step_rejects_host_pointers(handles):
+    rng = np.random.default_rng(0)
+    C = rng.uniform(size=(4, 5)); a = np.full(4, 0.25); b = np.full(5, 0.2)
+    pr = pins.make_problem("dense", a, b, C=C)
+    import torch
+    F = torch.zeros(4, dtype=torch.float64, device="cuda")
+    G = torch.zeros(5, dtype=torch.float64, device="cuda")
+    assert pins.pins_step_sinkhorn(handles["fp64"].h, pr.prob, 1.0, 1, F, G, None) == \
+        pins.PINS_ERR_INVALID_ARG
