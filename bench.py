@@ -103,6 +103,40 @@ def measured_peaks():
         return {}
 
 
+# kernel classes that stream the m x n matrix once per launch
+MN_CLASSES = ("row_lse", "col_lse", "marginals", "trial", "key_hist", "key_compact",
+              "csr_write", "certificate")
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure is measured by the driver)
+
+
+def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks):
+    """Roofline object for the class with the largest device time.
+
+    m x n passes: algorithmic bytes = m * n * elem_bytes (the cost matrix read once;
+    potentials and partials are O(m + n)); bound 'hbm' against the measured copy
+    bandwidth.  CG: algorithmic FP64 flops per iteration = 4 nnz + 14 (m + n)
+    (off-diagonal SpMV on the CSR and CSC copies, diagonal, three dot products and
+    four vector updates); bound 'alu' against the nominal FP64 rate."""
+    dom, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    if cnt == 0:
+        return None, dom
+    t = ms / cnt / 1e3
+    if dom == "cg":
+        per_launch = (4.0 * nnz + 14.0 * (m + n)) * (cg_iters / max(cnt, 1))
+        achieved = per_launch / t / 1e12
+        return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 (recipe table)", "avg_launch_us": t * 1e6,
+                "launches": cnt}, dom
+    per_launch = float(m) * n * elem_bytes
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = per_launch / t / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "avg_launch_us": t * 1e6, "launches": cnt}, dom
+
+
 def workload(args):
     from paper_2502_03749_gb300 import workloads as wl
     return wl.gmm_instance(0, m=args.n, n=args.n, eta=args.eta)
@@ -113,8 +147,8 @@ def config_dict(args, w):
                         f"Dirichlet(1) marginals, eta={args.eta}",
             "m": args.n, "n": args.n, "eta": args.eta, "K": args.K, "T1": 100, "T2": 50,
             "sparsify_gamma": args.gamma, "precision": args.prec,
-            "l2_note": "C is 64 MiB FP32 (mixed) / 128 MiB FP64: larger than or close to the "
-                       "126 MiB L2; no flush between steps",
+            "l2_note": "C is 64 MiB FP32 (mixed) / 128 MiB FP64; L2 flushed (256 MiB write) "
+                       "between timed steps; one step is a whole solve (~1e4 passes over C)",
             "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
 
 
@@ -202,7 +236,7 @@ def run_ours(args):
     pdev = pins.make_problem("dense", ad, bd, C=Cd, on_device=True)
     stream = torch.cuda.Stream()
     cfg = dict(prec=args.prec, eta=args.eta, K=args.K, sparsify_gamma=args.gamma,
-               device=local, cuda_stream=stream.cuda_stream)
+               device=local, cuda_stream=stream.cuda_stream, profile=1)
     h = pins.Pins(**cfg)
     res = pins.pins_result()
 
@@ -219,13 +253,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
+    cg_iters = 0
+    pins.pins_profile_read(h.h, reset=True)
     with ClockSampler(local) as clk:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         ev0.record(stream)
         for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                 # L2 flush between timed steps
             out = step()
             launches += out["gpu_launches"]
+            cg_iters += out["cg_iters"]
         ev1.record(stream)
         torch.cuda.synchronize()
+    prof = pins.pins_profile_read(h.h, reset=True)
     if world > 1:
         torch.distributed.barrier()
     t = ev0.elapsed_time(ev1) / 1e3
@@ -293,6 +334,12 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "fp64_gpu": fp64,
             "peaks_source": "MEASURED_PEAKS.json" if peaks else "fallback"}
+    keep = int(min(args.n * args.n, max(1, round(args.gamma * (2 * args.n - 1)))))
+    roof, dom = roofline(prof, args.n, args.n, 4 if args.prec == "mixed" else 8, cg_iters,
+                         keep, peaks)
+    line["roofline"] = roof
+    tot = sum(v[0] for v in prof.values()) or 1.0
+    line["kernel_time_share"] = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
     if world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(args, w)
     print(json.dumps(line), flush=True)

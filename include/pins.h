@@ -105,6 +105,8 @@ typedef struct {
   int queue_capacity;   /* serving: admitted-but-not-started requests */
   size_t device_mem_budget; /* serving: bytes of device workspace admission may
                                reserve; 0 = 80% of free memory at create time */
+  int profile;          /* 1: time every kernel class of the blocking solver with
+                           CUDA events (see pins_profile_read); 0 = off */
 } pins_config;
 
 typedef struct {
@@ -174,6 +176,19 @@ pins_status pins_poll(pins_handle* h, uint64_t ticket, pins_result* r);
 
 /* Serving: blocks until the ticket finishes, then behaves as pins_poll. */
 pins_status pins_wait(pins_handle* h, uint64_t ticket, pins_result* r);
+
+/* Profiling of the blocking solver (pins_solve and the step entry points) when
+ * the handle was created with cfg.profile = 1.  Each kernel launch is bracketed
+ * by CUDA events on the solver's stream; durations are accumulated per class.
+ * pins_profile_read copies min(n, pins_profile_classes()) entries of device
+ * milliseconds (ms) and launch counts (launches; either may be NULL), then
+ * clears the totals if reset != 0.  Classes: 0 row_lse, 1 col_lse,
+ * 2 marginals, 3 trial, 4 key_hist, 5 key_compact, 6 select, 7 csr_write,
+ * 8 csc, 9 cg, 10 certificate, 11 vector. */
+int pins_profile_classes(void);
+const char* pins_profile_name(int k);
+pins_status pins_profile_read(pins_handle* h, double* ms, long long* launches, int n,
+                              int reset);
 
 /* ------------------------------------------------------------------------- */
 /* Step-level entry points.  Each runs one hot-path step on device pointers,  */

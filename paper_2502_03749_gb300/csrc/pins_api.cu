@@ -152,6 +152,7 @@ extern "C" pins_status pins_create(const pins_config* cfg, pins_handle** out) {
   cudaMemcpy(h->exp_table, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice);
   h->solver.reset(new Solver(h->device, h->sms, h->exp_table));
   h->solver->set_stream(h->stream);
+  h->solver->set_profile(cfg->profile != 0);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   h->budget = cfg->device_mem_budget ? cfg->device_mem_budget : (size_t)(0.8 * (double)freeb);
@@ -174,6 +175,17 @@ extern "C" void pins_destroy(pins_handle* h) {
   if (h->exp_table) cudaFree(h->exp_table);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+extern "C" int pins_profile_classes(void) { return Solver::PC_COUNT; }
+
+extern "C" const char* pins_profile_name(int k) { return Solver::prof_name(k); }
+
+extern "C" pins_status pins_profile_read(pins_handle* h, double* ms, long long* launches, int n,
+                                         int reset) {
+  if (!h || n < 0) return PINS_ERR_INVALID_ARG;
+  h->solver->prof_read(ms, launches, n, reset != 0);
+  return PINS_OK;
 }
 
 extern "C" const char* pins_last_error(pins_handle* h) {

@@ -141,6 +141,17 @@ __device__ __forceinline__ dd dd_expm1(float th, float tl, const float2* __restr
 // ------------------------------------------------------------------------- //
 // warp / block reductions
 // ------------------------------------------------------------------------- //
+// double-float butterfly sum (every lane gets the total; fixed order)
+__device__ __forceinline__ dd warp_dd_sum(dd v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = dd_add(v, w);
+  }
+  return v;
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -160,6 +171,24 @@ __device__ __forceinline__ double warp_mind(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+// float pairs stored raw in an 8-byte partial slot (mixed policy: no FP64 ops)
+__device__ __forceinline__ void store_f2(double* slot, float x, float y) {
+  *reinterpret_cast<float2*>(slot) = make_float2(x, y);
+}
+__device__ __forceinline__ float2 load_f2(const double* slot) {
+  return *reinterpret_cast<const float2*>(slot);
+}
+__device__ __forceinline__ float2 load_f2_cg(const double* slot) {
+  double v = __ldcg(slot);
+  return *reinterpret_cast<float2*>(&v);
+}
+// FP32 LSE pair merge
+__device__ __forceinline__ void lse_merge_f(float& m1, float& s1, float m2, float s2) {
+  if (m2 == -INFINITY) return;
+  if (m1 == -INFINITY) { m1 = m2; s1 = s2; return; }
+  if (m2 > m1) { s1 = s1 * exp2f((m1 - m2) * 1.4426950408889634f) + s2; m1 = m2; }
+  else { s1 = s1 + s2 * exp2f((m2 - m1) * 1.4426950408889634f); }
 }
 // LSE pair merge: (m1, s1) <- (m1, s1) (+) (m2, s2); m = -inf means empty
 __device__ __forceinline__ void lse_merge(double& m1, double& s1, double m2, double s2) {

@@ -22,25 +22,27 @@ struct PassSet {
                cudaStream_t);
   void (*key_hist)(const PassArgs&, const SparsifyState*, unsigned int* hist, int blocks,
                    cudaStream_t);
-  void (*key_compact)(const PassArgs&, SparsifyState*, double* coo_key, long long* coo_idx,
-                      double* cand_key, long long* cand_idx, int coo_cap, int blocks,
-                      cudaStream_t);
+  void (*key_compact)(const PassArgs&, SparsifyState*, double* cand_key, long long* cand_idx,
+                      int* rowcnt, int blocks, cudaStream_t);
+  void (*key_write)(const PassArgs&, const SparsifyState*, const int* indptr, int* indices,
+                    double* data, int blocks, cudaStream_t);
 };
 
 const PassSet* passes_f64(int kind);
 const PassSet* passes_mixed(int kind);
+
+#define PINS_CSC_CHUNKS 256
 
 // sparse/vector launchers (pins_sparse.cu, pins_select.cu)
 struct SparseWS {
   int* rowcnt; int* colcnt;     // m, n
   int* indptr; int* indices; double* data;    // CSR: m+1, cap, cap
   int* colptr; int* rowidx; double* cdata;    // CSC: n+1, cap, cap
+  int* chunkcnt;                // PINS_CSC_CHUNKS * n
 };
-void build_csr(const long long* coo_idx, const double* coo_key, int nnz, int m, int n,
-               double key_scale, const SparseWS& sw, cudaStream_t st);
-void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m,
-                        int n, int* colcnt, int* colptr, int* rowidx, double* cdata,
-                        cudaStream_t st);
+void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
+                        int nnz, const SparseWS& sw, cudaStream_t st);
+void launch_scan(int* cnt, int* ptr, int len, cudaStream_t st);
 cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* c,
                        const int* indptr, const int* indices, const double* data,
                        const int* colptr, const int* rowidx, const double* cdata,
@@ -48,6 +50,13 @@ cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* 
                        double* part, double rtol, int max_iter, double* info, int sms,
                        cudaStream_t st);
 int cg_blocks(int N, int sms);
+// single-reduction cluster PCG (pins_cg.cu); *used = false when the system does
+// not fit one cluster's shared memory
+cudaError_t launch_pcg_cluster(int m, int n, double eta, const double* r, const double* c,
+                               const int* indptr, const int* indices, const double* data,
+                               const int* colptr, const int* rowidx, const double* cdata,
+                               const double* rhs, double* x, double rtol, int max_iter,
+                               double* info, int* flag, cudaStream_t st, bool* used);
 void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
 void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,
@@ -72,7 +81,6 @@ void launch_f2d(const float* x, double* y, size_t N, cudaStream_t st);
 // sparsify selection (pins_select.cu)
 void launch_key_select(SparsifyState* st, unsigned int* hist, long long total, cudaStream_t s);
 cudaError_t launch_cand_select(SparsifyState* st, const double* cand_key,
-                               const long long* cand_idx, double* coo_key, long long* coo_idx,
-                               int coo_cap, cudaStream_t s);
+                               const long long* cand_idx, int n, int* rowcnt, cudaStream_t s);
 
 }  // namespace pins

@@ -1,6 +1,6 @@
 // Instantiates the pass kernels for one arithmetic policy and every cost kind.
 // Included once per policy translation unit with PINS_POLICY and PINS_PASSES_FN set.
-#include "pins_passes.cuh"
+#include "pins_sparsify.cuh"
 #include "pins_kernels.h"
 
 namespace pins {
@@ -34,11 +34,16 @@ template <int K> struct Launch {
     k_key_hist<P><<<blocks, PINS_TPB, 0, st>>>(p, s, hist);
   }
   static void key_compact(const PassArgs& p, SparsifyState* s, double* ck, long long* ci,
-                          double* dk, long long* di, int cap, int blocks, cudaStream_t st) {
-    k_key_compact<P><<<blocks, PINS_TPB, 0, st>>>(p, s, ck, ci, dk, di, cap);
+                          int* rowcnt, int blocks, cudaStream_t st) {
+    k_key_compact<P><<<blocks, PINS_TPB, 0, st>>>(p, s, ck, ci, rowcnt);
+  }
+  static void key_write(const PassArgs& p, const SparsifyState* s, const int* indptr, int* indices,
+                        double* data, int blocks, cudaStream_t st) {
+    k_key_write<P><<<blocks, PINS_TPB, 0, st>>>(p, s, indptr, indices, data);
   }
   static const PassSet* get() {
-    static const PassSet ps = {P::MIXED, row_lse, col_lse, marg, cert, key_hist, key_compact};
+    static const PassSet ps = {P::MIXED, row_lse, col_lse, marg, cert, key_hist, key_compact,
+                               key_write};
     return &ps;
   }
 };

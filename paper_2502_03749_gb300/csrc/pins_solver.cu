@@ -64,7 +64,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.rt = cv.take<double>(m); w.ct = cv.take<double>(n);
   w.Pt64 = cv.take<double>(m); w.Qt64 = cv.take<double>(n);
   w.grad = cv.take<double>(N); w.dir = cv.take<double>(N);
-  w.cg_res = cv.take<double>(N); w.cg_p = cv.take<double>(N); w.cg_q = cv.take<double>(N);
+  w.cg_res = cv.take<double>(N); w.cg_p = cv.take<double>(N); w.cg_q = cv.take<double>(2 * (size_t)N);
   w.ab = cv.take<double>(N);
   w.xs = cv.take<double>(m); w.u = cv.take<double>(m); w.rr = cv.take<double>(m);
   w.cr = cv.take<double>(m); w.cp = cv.take<double>(m); w.tc = cv.take<double>(m);
@@ -87,8 +87,8 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.mws.cnt_all = cv.take<unsigned int>(1);
   w.st = cv.take<SparsifyState>(1);
   w.hist = cv.take<unsigned int>(PINS_HIST_NB + 1);
-  w.coo_key = cv.take<double>(kcap); w.coo_idx = cv.take<long long>(kcap);
   w.cand_key = cv.take<double>(PINS_CAND_CAP); w.cand_idx = cv.take<long long>(PINS_CAND_CAP);
+  w.sw.chunkcnt = cv.take<int>((size_t)PINS_CSC_CHUNKS * n);
   w.sw.rowcnt = cv.take<int>(m); w.sw.colcnt = cv.take<int>(n);
   w.sw.indptr = cv.take<int>(m + 1); w.sw.indices = cv.take<int>(kcap);
   w.sw.data = cv.take<double>(kcap);
@@ -123,7 +123,57 @@ Solver::Solver(int device, int sms, const float2* exp_table)
 
 Solver::~Solver() { release(); }
 
+const char* Solver::prof_name(int k) {
+  static const char* names[PC_COUNT] = {"row_lse", "col_lse", "marginals", "trial", "key_hist",
+                                        "key_compact", "select", "csr_write", "csc", "cg",
+                                        "certificate", "vector"};
+  return (k >= 0 && k < PC_COUNT) ? names[k] : "";
+}
+
+void Solver::prof_begin(int cls) {
+  if (!profile_) return;
+  while ((int)ev_pool_.size() < ev_next_ + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ev_pool_.push_back(e);
+  }
+  cudaEventRecord(ev_pool_[ev_next_], stream_);
+  ev_pending_.push_back(std::make_pair(cls, ev_next_));
+  ev_next_ += 2;
+}
+
+void Solver::prof_end() {
+  if (!profile_ || ev_pending_.empty()) return;
+  cudaEventRecord(ev_pool_[ev_pending_.back().second + 1], stream_);
+}
+
+void Solver::prof_drain() {
+  for (auto& pr : ev_pending_) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev_pool_[pr.second], ev_pool_[pr.second + 1]) == cudaSuccess) {
+      prof_ms_[pr.first] += ms;
+      prof_cnt_[pr.first] += 1;
+    }
+  }
+  cudaGetLastError();
+  ev_pending_.clear();
+  ev_next_ = 0;
+}
+
+void Solver::prof_read(double* ms, long long* cnt, int n, bool reset) {
+  for (int k = 0; k < n && k < PC_COUNT; ++k) {
+    if (ms) ms[k] = prof_ms_[k];
+    if (cnt) cnt[k] = prof_cnt_[k];
+  }
+  if (reset)
+    for (int k = 0; k < PC_COUNT; ++k) { prof_ms_[k] = 0.0; prof_cnt_[k] = 0; }
+}
+
 void Solver::release() {
+  for (auto e : ev_pool_) cudaEventDestroy(e);
+  ev_pool_.clear();
+  ev_pending_.clear();
+  ev_next_ = 0;
   if (ws_.base) cudaFree(ws_.base);
   ws_ = Workspace();
   if (h_scal_) cudaFreeHost(h_scal_);
@@ -147,6 +197,7 @@ pins_status Solver::sync(const char* where) {
     err_ = std::string(where) + ": " + cudaGetErrorString(e);
     return PINS_ERR_CUDA;
   }
+  if (profile_) prof_drain();
   return PINS_OK;
 }
 
@@ -346,70 +397,98 @@ PassArgs Solver::args(double s, const double* F, const double* G) {
 
 void Solver::prep(double s) {
   // (called with the solver's own F, G)
+  prof_begin(PC_VEC);
   launch_prep(ws_.F, ws_.G, m_, n_, eta_, s, mixed_ ? nullptr : ws_.A64,
               mixed_ ? nullptr : ws_.B64, mixed_ ? ws_.Add : nullptr, mixed_ ? ws_.Bdd : nullptr,
               stream_);
+  prof_end();
   ++launches_;
 }
 
 void Solver::sinkhorn_iter(double s, int t) {
   prep(s);
   PassArgs pa = args(s, ws_.F, ws_.G);
+  prof_begin(PC_ROW_LSE);
   ps_->row_lse(pa, geom_, ws_.mws, ws_.F, ws_.scal + SC_ROWRES + t, stream_);
+  prof_end();
   prep(s);
+  prof_begin(PC_COL_LSE);
   ps_->col_lse(pa, geom_, ws_.mws, ws_.G, stream_);
+  prof_end();
   launches_ += 2;
 }
 
 void Solver::marg(double s, bool trial) {
   PassArgs pa = args(s, ws_.F, ws_.G);
+  prof_begin(trial ? PC_TRIAL : PC_MARG);
   if (trial) {
     TrialArgs tr{ws_.Pt64, ws_.Qt64, ws_.Ptdd, ws_.Qtdd};
     ps_->marg(pa, geom_, ws_.mws, &tr, ws_.rt, ws_.ct, ws_.scal + SC_TRIAL, stream_);
   } else {
     ps_->marg(pa, geom_, ws_.mws, nullptr, ws_.r, ws_.c, ws_.scal + SC_MARG, stream_);
   }
+  prof_end();
   ++launches_;
 }
 
 pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out) {
+  // window: 64 nats of z below the largest key (X~ ratio e^-64), widened or
+  // refined by the select kernel until the threshold bin fits the candidates
   SparsifyState st{};
+  double width;
   if (!mixed_) {
     st.kref = eta_ * zmax + 1e-9 * (1.0 + s + std::fabs(eta_ * zmax));
-    st.width = 64.0 * eta_ / PINS_HIST_NB;
+    width = 64.0 * eta_ / PINS_HIST_NB;
   } else {
     st.kref = zmax + 1e-3 * (1.0 + std::fabs(zmax));
-    st.width = 64.0 / PINS_HIST_NB;
+    width = 64.0 / PINS_HIST_NB;
   }
-  st.lo = 0.0; st.count_in = 0; st.level = 0; st.done = 0; st.need = 0; st.thr_bin = -1;
-  st.cand_count = 0; st.coo_count = 0; st.overflow = 0; st.keep = keep;
+  st.inv_width = 1.0 / width;
+  st.kref_f = (float)st.kref;
+  st.inv_width_f = (float)st.inv_width;
+  st.lo = 0.0; st.lo_f = 0.0f; st.count_in = 0; st.level = 0; st.done = 0; st.need = 0;
+  st.thr_bin = -1; st.cand_count = 0; st.overflow = 0; st.keep = keep;
   st.tau = 0.0; st.tau_idx = -1;
-  // SparsifyState sits in pinned memory space of h_scal_? keep a local copy
   cudaMemcpyAsync(ws_.st, &st, sizeof(st), cudaMemcpyHostToDevice, stream_);
+  cudaMemsetAsync(ws_.sw.rowcnt, 0, sizeof(int) * m_, stream_);
   PassArgs pa = args(s, ws_.F, ws_.G);
   int blocks = std::min(std::max((m_ + 7) / 8, 1), sms_ * 8);
-  SparsifyState hs{};
+  SparsifyState* hs = reinterpret_cast<SparsifyState*>(h_scal_ + SC_STATE);
   for (int round = 0; round < 13; ++round) {
+    prof_begin(PC_HIST);
     ps_->key_hist(pa, ws_.st, ws_.hist, blocks, stream_);
+    prof_end();
+    prof_begin(PC_SELECT);
     launch_key_select(ws_.st, ws_.hist, (long long)m_ * n_, stream_);
-    ps_->key_compact(pa, ws_.st, ws_.coo_key, ws_.coo_idx, ws_.cand_key, ws_.cand_idx,
-                     ws_.kcap, blocks, stream_);
-    if (launch_cand_select(ws_.st, ws_.cand_key, ws_.cand_idx, ws_.coo_key, ws_.coo_idx,
-                           ws_.kcap, stream_) != cudaSuccess) {
+    prof_end();
+    prof_begin(PC_COMPACT);
+    ps_->key_compact(pa, ws_.st, ws_.cand_key, ws_.cand_idx, ws_.sw.rowcnt, blocks, stream_);
+    prof_end();
+    prof_begin(PC_SELECT);
+    cudaError_t cse = launch_cand_select(ws_.st, ws_.cand_key, ws_.cand_idx, n_, ws_.sw.rowcnt, stream_);
+    prof_end();
+    if (cse !=
+        cudaSuccess) {
       return check("sparsify select");
     }
     launches_ += 4;
-    cudaMemcpyAsync(&hs, ws_.st, sizeof(hs), cudaMemcpyDeviceToHost, stream_);
+    cudaMemcpyAsync(hs, ws_.st, sizeof(SparsifyState), cudaMemcpyDeviceToHost, stream_);
     pins_status e = sync("sparsify");
     if (e != PINS_OK) return e;
-    if (hs.done) break;
+    if (hs->done) break;
   }
-  if (!hs.done || hs.overflow || (int)hs.coo_count != keep) {
+  if (!hs->done || hs->overflow) {
     err_ = "sparsify: threshold selection failed (more tied keys than the candidate buffer)";
     return PINS_ERR_CUDA;
   }
-  build_csr(ws_.coo_idx, ws_.coo_key, keep, m_, n_, mixed_ ? 1.0 : 1.0 / eta_, ws_.sw, stream_);
-  launches_ += 7;
+  prof_begin(PC_WRITE);
+  launch_scan(ws_.sw.rowcnt, ws_.sw.indptr, m_, stream_);
+  ps_->key_write(pa, ws_.st, ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, blocks, stream_);
+  prof_end();
+  prof_begin(PC_CSC);
+  build_csc_from_csr(ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, m_, n_, keep, ws_.sw, stream_);
+  prof_end();
+  launches_ += 6;
   *nnz_out = keep;
   return check("csr");
 }
@@ -420,11 +499,13 @@ pins_status Solver::certificate(double s) {
   PassArgs pa = args(s, ws_.F, ws_.G);
   CertArgs ca{ws_.xs, ws_.ys, ws_.u, ws_.v, ws_.ec, ws_.c1, ws_.v, ws_.rr, ws_.cr, ws_.cp,
               ws_.tc, ws_.u2};
+  prof_begin(PC_CERT);
   ps_->cert(pa, geom_, ws_.mws, ca, true, stream_);
   launch_cert_mid(b_, ws_.c1, n_, ws_.ys, ws_.ec, stream_);
   ps_->cert(pa, geom_, ws_.mws, ca, false, stream_);
   launch_cert_final(a_, b_, ws_.rr, ws_.cr, ws_.cp, ws_.tc, ws_.u2, ws_.v, m_, n_,
                     ws_.scal + SC_CERT, stream_);
+  prof_end();
   launches_ += 5;
   return check("certificate");
 }
@@ -486,11 +567,14 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       int nnz = 0;
       if ((stt = sparsify(s, keep, zmax, &nnz)) != PINS_OK) { r.status = stt; return stt; }
       launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
+      cudaMemsetAsync(ws_.cg_part + 3 * 64, 0, sizeof(double), stream_);   // CG index-check flag
+      prof_begin(PC_CG);
       cudaError_t ce = launch_pcg(m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
                                   ws_.sw.data, ws_.sw.colptr, ws_.sw.rowidx, ws_.sw.cdata,
                                   ws_.grad, ws_.dir, ws_.cg_res, ws_.cg_p, ws_.cg_q,
                                   ws_.cg_part, cfg.cg_rtol, max_cg, ws_.scal + SC_CG, sms_,
                                   stream_);
+      prof_end();
       if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
       launch_dot2(ws_.grad, ws_.dir, ws_.ab, ws_.dir, m + n, ws_.scal + SC_DOTS, stream_);
       launches_ += 3;
@@ -506,7 +590,17 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL, 16 * sizeof(double),
                         cudaMemcpyDeviceToHost, stream_);
         if ((stt = sync("line search")) != PINS_OK) { r.status = stt; return stt; }
-        if (q == 0) r.cg_iters += (int)h_scal_[SC_CG];
+        if (q == 0) {
+          r.cg_iters += (int)h_scal_[SC_CG];
+          int flag = 0;
+          cudaMemcpy(&flag, ws_.cg_part + 3 * 64, sizeof(int), cudaMemcpyDeviceToHost);
+          if (flag) {
+            err_ = "cg: an index outside the cluster's slices was skipped (flag " +
+                   std::to_string(flag) + ")";
+            r.status = PINS_ERR_CUDA;
+            return PINS_ERR_CUDA;
+          }
+        }
         const double gtd = h_scal_[SC_DOTS + 0];
         const double adot = h_scal_[SC_DOTS + 1];
         const double dsum = h_scal_[SC_TRIAL + 3];
@@ -643,8 +737,7 @@ pins_status Solver::step_cg(int m, int n, double eta, const double* r, const dou
   if (m < 1 || n < 1 || nnz < 0 || !(eta > 0.0) || max_iter < 0) { err_ = "bad CG arguments"; return PINS_ERR_INVALID_ARG; }
   pins_status st = ensure(m, n, std::max(nnz, 1), 1, PINS_COST_GRID_SQEUCLID, false, false, 1);
   if (st != PINS_OK) return st;
-  build_csc_from_csr(indptr, indices, data, m, n, ws_.sw.colcnt, ws_.sw.colptr, ws_.sw.rowidx,
-                     ws_.sw.cdata, stream_);
+  build_csc_from_csr(indptr, indices, data, m, n, nnz, ws_.sw, stream_);
   cudaError_t ce = launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
                               ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p,
                               ws_.cg_q, ws_.cg_part, rtol, max_iter, info, sms_, stream_);

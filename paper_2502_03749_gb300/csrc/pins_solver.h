@@ -5,7 +5,7 @@
 #include <vector>
 #include "../../include/pins.h"
 #include "pins_kernels.h"
-#include "pins_passes.cuh"
+#include "pins_sparsify.cuh"
 
 namespace pins {
 
@@ -22,7 +22,7 @@ struct Workspace {
   MergeWS mws;
   SparsifyState* st;
   unsigned int* hist;
-  double* coo_key; long long* coo_idx; double* cand_key; long long* cand_idx;
+  double* cand_key; long long* cand_idx;
   SparseWS sw;
   double* cg_part;
   double* scal;            // device scalars (see Solver::SC_*)
@@ -37,7 +37,9 @@ size_t workspace_bytes(int m, int n, int kcap, int t1cap, int cost_kind, bool mi
 class Solver {
  public:
   // scalar slots in Workspace::scal (doubles)
-  enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_ROWRES = 32 };
+  // (SC_STATE: 12 doubles of pinned host memory receive the SparsifyState)
+  enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_STATE = 18,
+         SC_ROWRES = 32 };
 
   Solver(int device, int sms, const float2* exp_table);
   ~Solver();
@@ -73,7 +75,25 @@ class Solver {
   const std::string& error() const { return err_; }
   long long launches() const { return launches_; }
 
+  // Optional per-kernel-class device timing: CUDA events recorded on the
+  // solver's stream around each launch, drained at every host sync.
+  enum { PC_ROW_LSE = 0, PC_COL_LSE, PC_MARG, PC_TRIAL, PC_HIST, PC_COMPACT, PC_SELECT,
+         PC_WRITE, PC_CSC, PC_CG, PC_CERT, PC_VEC, PC_COUNT };
+  static const char* prof_name(int k);
+  void set_profile(bool on) { profile_ = on; }
+  void prof_read(double* ms, long long* cnt, int n, bool reset);
+
  private:
+  void prof_begin(int cls);
+  void prof_end();
+  void prof_drain();
+  bool profile_ = false;
+  std::vector<cudaEvent_t> ev_pool_;
+  std::vector<std::pair<int, int>> ev_pending_;   // (class, index of start event)
+  int ev_next_ = 0, ev_cls_ = -1;
+  double prof_ms_[PC_COUNT] = {};
+  long long prof_cnt_[PC_COUNT] = {};
+
   pins_status prepare(const pins_config& cfg, const pins_problem& p, bool need_kcap);
   pins_status ensure(int m, int n, int kcap, int t1cap, int kind, bool mixed, bool host_in, int d);
   pins_status upload(const pins_problem& p);

@@ -1,7 +1,11 @@
-// Sparse side of the Newton step (Algorithm 2): CSR/CSC assembly of the kept
+// Sparse side of the Newton step (Algorithm 2): CSC assembly of the kept
 // coupling entries, the truncated Jacobi-preconditioned CG on
 //   M d = rhs,   M = (1/eta) [[diag r, S], [S^T, diag c]],
 // and the O(m + n) vector kernels of the solver (FP64).
+//
+// FP64 on GB300 runs at ~1/64 of the FP32 rate (~19 SM-cycles per warp-wide FP64
+// instruction), so scalar bookkeeping is done by one thread and broadcast, and the
+// vector work is spread over a thread-block cluster.
 #include <cooperative_groups.h>
 #include "pins_kernels.h"
 
@@ -9,21 +13,7 @@ namespace cg = cooperative_groups;
 
 namespace pins {
 
-// ------------------------------------------------------------------------- //
-// CSR / CSC assembly from the COO list of kept entries (linear index + key).
-// Positions inside a row (column) come from atomics, then each row (column) is
-// sorted by column (row) index, so the final arrays do not depend on timing.
-// ------------------------------------------------------------------------- //
-__global__ void k_coo_count(const long long* idx, int nnz, int n, int* rowcnt, int* colcnt) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
-    long long l = idx[e];
-    int i = (int)(l / n), j = (int)(l - (long long)i * n);
-    atomicAdd(rowcnt + i, 1);
-    atomicAdd(colcnt + j, 1);
-  }
-}
-
-// exclusive scan of cnt[0..len) into ptr[0..len], resets cnt to 0 (cursor)
+// exclusive scan of cnt[0..len) into ptr[0..len], resets cnt to 0
 __global__ void __launch_bounds__(1024) k_scan(int* cnt, int* ptr, int len) {
   __shared__ int sh[1024];
   __shared__ int carry;
@@ -47,81 +37,126 @@ __global__ void __launch_bounds__(1024) k_scan(int* cnt, int* ptr, int len) {
   }
   if (threadIdx.x == 0) ptr[len] = carry;
 }
-
-// value of a kept entry: X~_ij = exp(key / eta) (FP64 key) or exp(z) (mixed key = z)
-__global__ void k_coo_scatter(const long long* idx, const double* key, int nnz, int n,
-                              double key_scale, const int* rowptr, int* rowcur,
-                              int* csr_col, double* csr_val, const int* colptr, int* colcur,
-                              int* csc_row, double* csc_val) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x) {
-    long long l = idx[e];
-    int i = (int)(l / n), j = (int)(l - (long long)i * n);
-    double val = exp(key[e] * key_scale);
-    int pr = rowptr[i] + atomicAdd(rowcur + i, 1);
-    csr_col[pr] = j; csr_val[pr] = val;
-    int pc = colptr[j] + atomicAdd(colcur + j, 1);
-    csc_row[pc] = i; csc_val[pc] = val;
-  }
-}
-
-// insertion sort of each segment by index (segments are short: ~2 entries)
-__global__ void k_segment_sort(const int* ptr, int len, int* ind, double* val) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < len; s += gridDim.x * blockDim.x) {
-    int lo = ptr[s], hi = ptr[s + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-      int ki = ind[a]; double kv = val[a];
-      int b = a - 1;
-      while (b >= lo && ind[b] > ki) { ind[b + 1] = ind[b]; val[b + 1] = val[b]; --b; }
-      ind[b + 1] = ki; val[b + 1] = kv;
-    }
-  }
-}
-
-void build_csr(const long long* coo_idx, const double* coo_key, int nnz, int m, int n,
-               double key_scale, const SparseWS& sw, cudaStream_t st) {
-  cudaMemsetAsync(sw.rowcnt, 0, sizeof(int) * m, st);
-  cudaMemsetAsync(sw.colcnt, 0, sizeof(int) * n, st);
-  int blocks = (nnz + 255) / 256; if (blocks < 1) blocks = 1; if (blocks > 1024) blocks = 1024;
-  k_coo_count<<<blocks, 256, 0, st>>>(coo_idx, nnz, n, sw.rowcnt, sw.colcnt);
-  k_scan<<<1, 1024, 0, st>>>(sw.rowcnt, sw.indptr, m);
-  k_scan<<<1, 1024, 0, st>>>(sw.colcnt, sw.colptr, n);
-  k_coo_scatter<<<blocks, 256, 0, st>>>(coo_idx, coo_key, nnz, n, key_scale, sw.indptr,
-                                        sw.rowcnt, sw.indices, sw.data, sw.colptr, sw.colcnt,
-                                        sw.rowidx, sw.cdata);
-  k_segment_sort<<<(m + 255) / 256, 256, 0, st>>>(sw.indptr, m, sw.indices, sw.data);
-  k_segment_sort<<<(n + 255) / 256, 256, 0, st>>>(sw.colptr, n, sw.rowidx, sw.cdata);
-}
-
-// CSC from a given CSR (for the step-level CG entry point)
-__global__ void k_csr_count_cols(const int* indptr, const int* indices, int m, int* colcnt) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    for (int e = indptr[i]; e < indptr[i + 1]; ++e) atomicAdd(colcnt + indices[e], 1);
-}
-__global__ void k_csr_scatter_cols(const int* indptr, const int* indices, const double* data,
-                                   int m, const int* colptr, int* colcur, int* rowidx,
-                                   double* cdata) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    for (int e = indptr[i]; e < indptr[i + 1]; ++e) {
-      int j = indices[e];
-      int pc = colptr[j] + atomicAdd(colcur + j, 1);
-      rowidx[pc] = i; cdata[pc] = data[e];
-    }
-}
-void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m,
-                        int n, int* colcnt, int* colptr, int* rowidx, double* cdata,
-                        cudaStream_t st) {
-  cudaMemsetAsync(colcnt, 0, sizeof(int) * n, st);
-  k_csr_count_cols<<<(m + 255) / 256, 256, 0, st>>>(indptr, indices, m, colcnt);
-  k_scan<<<1, 1024, 0, st>>>(colcnt, colptr, n);
-  k_csr_scatter_cols<<<(m + 255) / 256, 256, 0, st>>>(indptr, indices, data, m, colptr, colcnt,
-                                                      rowidx, cdata);
-  k_segment_sort<<<(n + 255) / 256, 256, 0, st>>>(colptr, n, rowidx, cdata);
+void launch_scan(int* cnt, int* ptr, int len, cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(cnt, ptr, len);
 }
 
 // ------------------------------------------------------------------------- //
-// Truncated PCG (Jacobi), cooperative: a few CTAs, grid-wide barriers.
-// Reduction order is fixed (per-thread strided sums, block tree, partials summed
-// in block order by every CTA), so every CTA sees identical scalars.
+// CSC from the row-ordered CSR.  Up to PINS_CSC_SMEM entries: one CTA sorts the
+// keys (j << 32 | i) by a bitonic network in shared memory (payload: CSR
+// position) and derives colptr from the sorted columns.  Larger: a stable
+// counting sort over row chunks.  Either way the rows of a column come out
+// ascending, independent of timing.
+// ------------------------------------------------------------------------- //
+#define PINS_CSC_SMEM 16384
+
+__global__ void __launch_bounds__(1024)
+k_csc_sort(const int* indptr, const int* indices, const double* data, int m, int n,
+           int* colptr, int* rowidx, double* cdata) {
+  extern __shared__ unsigned char csc_smem[];
+  const int K = indptr[m];
+  unsigned int P2 = 1;
+  while (P2 < (unsigned int)K) P2 <<= 1;
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(csc_smem);
+  int* pos = reinterpret_cast<int*>(key + P2);
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    for (int e = indptr[i]; e < indptr[i + 1]; ++e) {
+      key[e] = ((unsigned long long)(unsigned int)indices[e] << 32) | (unsigned int)i;
+      pos[e] = e;
+    }
+  for (unsigned int q = K + threadIdx.x; q < P2; q += blockDim.x) { key[q] = ~0ull; pos[q] = -1; }
+  __syncthreads();
+  for (unsigned int k = 2; k <= P2; k <<= 1) {
+    for (unsigned int jv = k >> 1; jv > 0; jv >>= 1) {
+      for (unsigned int t = threadIdx.x; t < P2; t += blockDim.x) {
+        unsigned int l = t ^ jv;
+        if (l > t) {
+          bool up = ((t & k) == 0);
+          unsigned long long ka = key[t], kb = key[l];
+          if (up ? (ka > kb) : (ka < kb)) {
+            key[t] = kb; key[l] = ka;
+            int pa = pos[t]; pos[t] = pos[l]; pos[l] = pa;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    const int j = (int)(key[q] >> 32);
+    rowidx[q] = (int)(key[q] & 0xffffffffu);
+    cdata[q] = data[pos[q]];
+    const int jprev = (q == 0) ? -1 : (int)(key[q - 1] >> 32);
+    for (int c = jprev + 1; c <= j; ++c) colptr[c] = q;      // columns starting here
+    if (q == K - 1) for (int c = j + 1; c <= n; ++c) colptr[c] = K;
+  }
+  if (K == 0) for (int c = threadIdx.x; c <= n; c += blockDim.x) colptr[c] = 0;
+}
+
+__device__ __forceinline__ void chunk_rows(int c, int chunks, int m, int& r0, int& r1) {
+  const int R = (m + chunks - 1) / chunks;
+  r0 = min(m, c * R);
+  r1 = min(m, r0 + R);
+}
+__global__ void k_csc_count(const int* indptr, const int* indices, int m, int n, int chunks,
+                            int* cnt) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += gridDim.x * blockDim.x) {
+    int r0, r1; chunk_rows(c, chunks, m, r0, r1);
+    for (int e = indptr[r0]; e < indptr[r1]; ++e) cnt[(size_t)c * n + indices[e]] += 1;
+  }
+}
+__global__ void k_csc_colscan(int* cnt, int chunks, int n, int* coltot) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int run = 0;
+    for (int c = 0; c < chunks; ++c) {
+      int v = cnt[(size_t)c * n + j];
+      cnt[(size_t)c * n + j] = run;
+      run += v;
+    }
+    coltot[j] = run;
+  }
+}
+__global__ void k_csc_scatter(const int* indptr, const int* indices, const double* data, int m,
+                              int n, int chunks, int* off, const int* colptr, int* rowidx,
+                              double* cdata) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += gridDim.x * blockDim.x) {
+    int r0, r1; chunk_rows(c, chunks, m, r0, r1);
+    for (int i = r0; i < r1; ++i)
+      for (int e = indptr[i]; e < indptr[i + 1]; ++e) {
+        const int j = indices[e];
+        const int pos = colptr[j] + off[(size_t)c * n + j]++;
+        rowidx[pos] = i;
+        cdata[pos] = data[e];
+      }
+  }
+}
+
+void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
+                        int nnz, const SparseWS& sw, cudaStream_t st) {
+  if (nnz <= PINS_CSC_SMEM) {
+    unsigned int P2 = 1;
+    while (P2 < (unsigned int)nnz) P2 <<= 1;
+    const size_t smem = (size_t)P2 * (sizeof(unsigned long long) + sizeof(int));
+    static bool configured = false;
+    if (!configured) {
+      cudaFuncSetAttribute(k_csc_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((size_t)PINS_CSC_SMEM * 12));
+      configured = true;
+    }
+    k_csc_sort<<<1, 1024, smem, st>>>(indptr, indices, data, m, n, sw.colptr, sw.rowidx, sw.cdata);
+    return;
+  }
+  const int chunks = m < PINS_CSC_CHUNKS ? m : PINS_CSC_CHUNKS;
+  cudaMemsetAsync(sw.chunkcnt, 0, sizeof(int) * (size_t)chunks * n, st);
+  k_csc_count<<<(chunks + 255) / 256, 256, 0, st>>>(indptr, indices, m, n, chunks, sw.chunkcnt);
+  k_csc_colscan<<<(n + 255) / 256, 256, 0, st>>>(sw.chunkcnt, chunks, n, sw.colcnt);
+  k_scan<<<1, 1024, 0, st>>>(sw.colcnt, sw.colptr, n);
+  k_csc_scatter<<<(chunks + 255) / 256, 256, 0, st>>>(indptr, indices, data, m, n, chunks,
+                                                      sw.chunkcnt, sw.colptr, sw.rowidx, sw.cdata);
+}
+
+// ------------------------------------------------------------------------- //
+// CG arguments (shared by the cluster and the cooperative kernels)
 // ------------------------------------------------------------------------- //
 struct CGArgs {
   int m, n; double inv_eta;
@@ -130,7 +165,8 @@ struct CGArgs {
   const int* colptr; const int* rowidx; const double* cdata;
   const double* rhs; double* x;
   double* res; double* p; double* q;
-  double* part;     // 3 * gridDim partials (see k_pcg)
+  double* part;     // 3 * gridDim partials (cooperative kernel)
+  double* dinv;     // D^-1 (cluster kernel)
   double rtol; int max_iter;
   double* info;     // {iterations, relative residual}
 };
@@ -149,8 +185,11 @@ __device__ __forceinline__ double cg_block_sum(double v, double* sh) {
   return t;  // thread 0
 }
 
+// ------------------------------------------------------------------------- //
+// Cooperative fallback (systems too large for one cluster's shared memory):
+// grid-wide barriers; scalars from per-block partials summed in block order.
+// ------------------------------------------------------------------------- //
 __device__ __forceinline__ double cg_apply(const CGArgs& a, const double* v, int t) {
-  // (M v)_t
   if (t < a.m) {
     double acc = a.r[t] * v[t];
     for (int e = a.indptr[t]; e < a.indptr[t + 1]; ++e) acc += a.data[e] * v[a.m + a.indices[e]];
@@ -161,17 +200,13 @@ __device__ __forceinline__ double cg_apply(const CGArgs& a, const double* v, int
   for (int e = a.colptr[j]; e < a.colptr[j + 1]; ++e) acc += a.cdata[e] * v[a.rowidx[e]];
   return acc * a.inv_eta;
 }
-__device__ __forceinline__ double cg_dinv(const CGArgs& a, int t) {
-  double d = (t < a.m) ? a.r[t] : a.c[t - a.m];
-  return 1.0 / (d * a.inv_eta);
-}
 
 __global__ void __launch_bounds__(256) k_pcg(CGArgs a) {
-  // partial slots: [0, G) <p, Mp>, [G, 2G) <res, res>, [2G, 3G) <res, D^-1 res>.
-  // A slot is rewritten only after a barrier that every reader of its previous
-  // contents has passed.
+  // partial slots: [0, G) <p, Mp>, [G, 2G) <res, res>, [2G, 3G) <res, D^-1 res>;
+  // a slot is rewritten only after a barrier every reader of it has passed.
   cg::grid_group grid = cg::this_grid();
   __shared__ double sh[32];
+  __shared__ double bc[4];
   const int N = a.m + a.n;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthr = gridDim.x * blockDim.x;
@@ -179,21 +214,28 @@ __global__ void __launch_bounds__(256) k_pcg(CGArgs a) {
   double l_rz = 0.0, l_bb = 0.0;
   for (int t = tid; t < N; t += nthr) {
     double rv = a.rhs[t];
-    a.x[t] = 0.0; a.res[t] = rv;
-    double z = cg_dinv(a, t) * rv;
+    double dg = (t < a.m) ? a.r[t] : a.c[t - a.m];
+    double di = 1.0 / (dg * a.inv_eta);
+    a.x[t] = 0.0; a.res[t] = rv; a.dinv[t] = di;
+    double z = di * rv;
     a.p[t] = z;
     l_rz += rv * z; l_bb += rv * rv;
   }
   double b0 = cg_block_sum(l_rz, sh);
+  __syncthreads();
   double b1 = cg_block_sum(l_bb, sh);
   if (threadIdx.x == 0) { a.part[2 * G + blockIdx.x] = b0; a.part[G + blockIdx.x] = b1; }
   grid.sync();
-  double rz = 0.0, bb = 0.0;
-  for (int k = 0; k < G; ++k) { rz += a.part[2 * G + k]; bb += a.part[G + k]; }
-  const double bnorm = sqrt(bb);
+  double rz = 0.0, bnorm = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < G; ++k) { rz += a.part[2 * G + k]; bnorm += a.part[G + k]; }
+    bnorm = sqrt(bnorm);
+    bc[2] = (bnorm > 0.0) ? 0.0 : 1.0;
+  }
+  __syncthreads();
   int it = 0;
-  double rel = (bnorm > 0.0) ? 1.0 : 0.0;
-  if (bnorm > 0.0) {
+  double rel = (bc[2] == 0.0) ? 1.0 : 0.0;
+  if (bc[2] == 0.0) {
     while (it < a.max_iter) {
       double l_pq = 0.0;
       for (int t = tid; t < N; t += nthr) {
@@ -204,31 +246,43 @@ __global__ void __launch_bounds__(256) k_pcg(CGArgs a) {
       double bp = cg_block_sum(l_pq, sh);
       if (threadIdx.x == 0) a.part[blockIdx.x] = bp;
       grid.sync();
-      double pq = 0.0;
-      for (int k = 0; k < G; ++k) pq += a.part[k];
-      double alpha = rz / pq;
+      if (threadIdx.x == 0) {
+        double pq = 0.0;
+        for (int k = 0; k < G; ++k) pq += a.part[k];
+        bc[0] = rz / pq;
+      }
+      __syncthreads();
+      const double alpha = bc[0];
       double l_rr = 0.0, l_rz2 = 0.0;
       for (int t = tid; t < N; t += nthr) {
         a.x[t] += alpha * a.p[t];
         double rv = a.res[t] - alpha * a.q[t];
         a.res[t] = rv;
         l_rr += rv * rv;
-        l_rz2 += rv * (cg_dinv(a, t) * rv);
+        l_rz2 += rv * (a.dinv[t] * rv);
       }
       double c0 = cg_block_sum(l_rr, sh);
+      __syncthreads();
       double c1 = cg_block_sum(l_rz2, sh);
       if (threadIdx.x == 0) { a.part[G + blockIdx.x] = c0; a.part[2 * G + blockIdx.x] = c1; }
       grid.sync();
-      double rr = 0.0, rz2 = 0.0;
-      for (int k = 0; k < G; ++k) { rr += a.part[G + k]; rz2 += a.part[2 * G + k]; }
       ++it;
-      rel = sqrt(rr) / bnorm;
-      if (!(rel > a.rtol)) break;   // also stops on NaN
-      double beta = rz2 / rz;
-      rz = rz2;
-      for (int t = tid; t < N; t += nthr) a.p[t] = cg_dinv(a, t) * a.res[t] + beta * a.p[t];
+      if (threadIdx.x == 0) {
+        double rr = 0.0, rz2 = 0.0;
+        for (int k = 0; k < G; ++k) { rr += a.part[G + k]; rz2 += a.part[2 * G + k]; }
+        rel = sqrt(rr) / bnorm;
+        bc[1] = rz2 / rz;
+        rz = rz2;
+        bc[2] = (rel > a.rtol) ? 0.0 : 1.0;
+        bc[3] = rel;
+      }
+      __syncthreads();
+      if (bc[2] != 0.0) break;
+      const double beta = bc[1];
+      for (int t = tid; t < N; t += nthr) a.p[t] = a.dinv[t] * a.res[t] + beta * a.p[t];
       grid.sync();
     }
+    rel = bc[3];
   }
   if (tid == 0) { a.info[0] = (double)it; a.info[1] = rel; }
 }
@@ -253,6 +307,13 @@ cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* 
   a.colptr = colptr; a.rowidx = rowidx; a.cdata = cdata;
   a.rhs = rhs; a.x = x; a.res = res; a.p = p; a.q = q; a.part = part;
   a.rtol = rtol; a.max_iter = max_iter; a.info = info;
+  bool used = false;
+  cudaError_t ce = launch_pcg_cluster(m, n, eta, r, c, indptr, indices, data, colptr, rowidx,
+                                      cdata, rhs, x, rtol, max_iter, info,
+                                      reinterpret_cast<int*>(part + 3 * 64), st, &used);
+  if (used) return ce;
+  const int N = m + n;
+  a.dinv = q + N;   // (the cooperative path uses p globally; D^-1 goes after q)
   int blocks = cg_blocks(m + n, sms);
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((void*)k_pcg, dim3(blocks), dim3(256), args, 0, st);
@@ -307,7 +368,7 @@ void launch_grad(const double* a, const double* b, const double* r, const double
   k_grad<<<blocks, 256, 0, st>>>(a, b, r, c, m, n, g);
 }
 
-// y[0..N) += alpha x  (F,G stacked as separate arrays)
+// (F, G) += alpha d
 __global__ void k_axpy2(double* F, double* G, const double* d, int m, int n, double alpha) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += gridDim.x * blockDim.x) {
     if (t < m) F[t] += alpha * d[t]; else G[t - m] += alpha * d[t];
@@ -336,10 +397,10 @@ void launch_outer(double* F, double* G, double* Phi, double* Psi, int m, int n, 
   k_outer<<<blocks, 256, 0, st>>>(F, G, Phi, Psi, m, n);
 }
 
-// deterministic dot products: out[0] = <x, y> (+ optional second pair)
-__global__ void __launch_bounds__(1024) k_dot2(const double* x1, const double* y1,
-                                               const double* x2, const double* y2, int N,
-                                               double* out) {
+// deterministic dot products: out[0] = <x1, y1>, out[1] = <x2, y2>
+__global__ void __launch_bounds__(256) k_dot2(const double* x1, const double* y1,
+                                              const double* x2, const double* y2, int N,
+                                              double* out) {
   __shared__ double sh[32];
   double s1 = 0.0, s2 = 0.0;
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
@@ -353,7 +414,7 @@ __global__ void __launch_bounds__(1024) k_dot2(const double* x1, const double* y
 }
 void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, int N,
                  double* out, cudaStream_t st) {
-  k_dot2<<<1, 1024, 0, st>>>(x1, y1, x2, y2, N, out);
+  k_dot2<<<1, 256, 0, st>>>(x1, y1, x2, y2, N, out);
 }
 
 // certificate helpers --------------------------------------------------------
@@ -376,11 +437,11 @@ __global__ void k_cert_mid(const double* b, const double* c1, int n, double* ys,
   }
 }
 // final scalars: cost, UB, LB, gap (one CTA, fixed order)
-__global__ void __launch_bounds__(1024) k_cert_final(const double* a, const double* b,
-                                                     const double* rr, const double* cr,
-                                                     const double* cp, const double* tc,
-                                                     const double* u2, const double* v,
-                                                     int m, int n, double* out4) {
+__global__ void __launch_bounds__(256) k_cert_final(const double* a, const double* b,
+                                                    const double* rr, const double* cr,
+                                                    const double* cp, const double* tc,
+                                                    const double* u2, const double* v,
+                                                    int m, int n, double* out4) {
   __shared__ double sh[32];
   double s_cost = 0, s_cr = 0, s_er = 0, s_ert = 0, s_lb = 0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -412,7 +473,7 @@ void launch_cert_mid(const double* b, const double* c1, int n, double* ys, doubl
 void launch_cert_final(const double* a, const double* b, const double* rr, const double* cr,
                        const double* cp, const double* tc, const double* u2, const double* v,
                        int m, int n, double* out4, cudaStream_t st) {
-  k_cert_final<<<1, 1024, 0, st>>>(a, b, rr, cr, cp, tc, u2, v, m, n, out4);
+  k_cert_final<<<1, 256, 0, st>>>(a, b, rr, cr, cp, tc, u2, v, m, n, out4);
 }
 
 // cast helpers

@@ -39,7 +39,8 @@ PINS_PREC_MIXED = 1
 EXPORTED = ["pins_config_default", "pins_create", "pins_destroy", "pins_last_error",
             "pins_solve", "pins_solve_batch", "pins_submit", "pins_poll", "pins_wait",
             "pins_step_sinkhorn", "pins_step_marginals", "pins_step_sparsify", "pins_step_cg",
-            "pins_step_objective_increase", "pins_step_certificate"]
+            "pins_step_objective_increase", "pins_step_certificate", "pins_profile_classes",
+            "pins_profile_name", "pins_profile_read"]
 
 
 class pins_config(ct.Structure):
@@ -50,7 +51,8 @@ class pins_config(ct.Structure):
                 ("max_backtrack", ct.c_int), ("sinkhorn_check_every", ct.c_int),
                 ("gap_every", ct.c_int), ("prec", ct.c_int), ("device", ct.c_int),
                 ("cuda_stream", ct.c_void_p), ("max_inflight", ct.c_int),
-                ("queue_capacity", ct.c_int), ("device_mem_budget", ct.c_size_t)]
+                ("queue_capacity", ct.c_int), ("device_mem_budget", ct.c_size_t),
+                ("profile", ct.c_int)]
 
 
 class pins_problem(ct.Structure):
@@ -107,9 +109,13 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.pins_step_objective_increase.argtypes = [P, ct.POINTER(pins_problem), D, P, P, P, P,
                                                  D, P]
     lib.pins_step_certificate.argtypes = [P, ct.POINTER(pins_problem), D, P, P, P]
+    lib.pins_profile_classes.argtypes = []
+    lib.pins_profile_name.argtypes = [I]
+    lib.pins_profile_read.argtypes = [P, P, P, I, I]
     for name in EXPORTED:
         if name not in ("pins_config_default", "pins_destroy", "pins_last_error"):
             getattr(lib, name).restype = ct.c_int
+    lib.pins_profile_name.restype = ct.c_char_p
     _lib = lib
     return lib
 
@@ -196,6 +202,23 @@ def pins_step_objective_increase(h, prob, s, F, G, df, dg, alpha, out) -> int:
 
 def pins_step_certificate(h, prob, s, F, G, out4) -> int:
     return load().pins_step_certificate(h, ct.byref(prob), s, _ptr(F), _ptr(G), _ptr(out4))
+
+
+def pins_profile_classes() -> int:
+    return load().pins_profile_classes()
+
+
+def pins_profile_name(k: int) -> str:
+    return load().pins_profile_name(k).decode()
+
+
+def pins_profile_read(h, reset: bool = False) -> dict:
+    """{class name: (device ms, launches)} of the handle's blocking solver."""
+    n = pins_profile_classes()
+    ms = (ct.c_double * n)()
+    cnt = (ct.c_longlong * n)()
+    load().pins_profile_read(h, ms, cnt, n, 1 if reset else 0)
+    return {pins_profile_name(k): (ms[k], cnt[k]) for k in range(n)}
 
 
 # --------------------------------------------------------------------------- #
