@@ -248,6 +248,35 @@ pins_status pins_step_certificate(pins_handle* h, const pins_problem* p,
                                   double s, const double* F, const double* G,
                                   double* out4);
 
+/* ------------------------------------------------------------------------- */
+/* Allocation-free marginal pass.  The paper has no counterpart: this entry   */
+/* serves callers that cannot allocate device memory (a host framework that   */
+/* owns all device memory through its own pool, a real-time loop that must    */
+/* not enter the driver's allocator, an embedding that reserves everything at */
+/* start-up).                                                                 */
+/* ------------------------------------------------------------------------- */
+#define PINS_NOALLOC_MAX_DIM 4096
+#define PINS_NOALLOC_SCRATCH_BYTES (3584u * 1024u)
+
+/* Same result as pins_step_marginals (row sums r, column sums c of the plan
+ * exp((F_i + G_j - s (C_ij + eta)) / eta); out3 = {l1 marginal residual, sum of
+ * the plan, max_ij (F_i + G_j - s (C_ij + eta))}), without a handle and without
+ * allocating: its scratch is a fixed static device array of
+ * PINS_NOALLOC_SCRATCH_BYTES that each GPU loading the library keeps until exit.
+ * Every pointer (p's arrays, F, G, r, c, out3) is a device pointer of the
+ * current device.  prec is PINS_PREC_FP64 (cost kinds DENSE_F64, POINTS, GRID)
+ * or PINS_PREC_MIXED (DENSE_F32, POINTS, GRID).  The work is queued on
+ * cuda_stream (NULL: the legacy default stream) and the call returns without
+ * waiting.  The first call on a device sets up that device's scratch (a symbol
+ * lookup and a small host-to-device copy): make it before any stream capture.
+ * All calls on a device share its scratch, so calls that overlap on the GPU
+ * race; order them on one stream.  Returns PINS_ERR_INVALID_ARG if m or n
+ * exceeds PINS_NOALLOC_MAX_DIM or an argument is invalid, PINS_ERR_CUDA if a
+ * CUDA call fails. */
+pins_status pins_marginals_noalloc(const pins_problem* p, double eta, int prec, double s,
+                                   const double* F, const double* G, double* r, double* c,
+                                   double* out3, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

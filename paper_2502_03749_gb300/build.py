@@ -22,6 +22,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I" + os.path.join(ROOT, "include")]
 
 SOURCES = ["pins_kernels_f64.cu", "pins_kernels_mixed.cu", "pins_sparse.cu", "pins_select.cu", "pins_cg.cu",
+           "pins_noalloc.cu",
            "pins_solver.cu", "pins_api.cu"]
 
 

@@ -40,7 +40,7 @@ EXPORTED = ["pins_config_default", "pins_create", "pins_destroy", "pins_last_err
             "pins_solve", "pins_solve_batch", "pins_submit", "pins_poll", "pins_wait",
             "pins_step_sinkhorn", "pins_step_marginals", "pins_step_sparsify", "pins_step_cg",
             "pins_step_objective_increase", "pins_step_certificate", "pins_profile_classes",
-            "pins_profile_name", "pins_profile_read"]
+            "pins_profile_name", "pins_profile_read", "pins_marginals_noalloc"]
 
 
 class pins_config(ct.Structure):
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.pins_profile_classes.argtypes = []
     lib.pins_profile_name.argtypes = [I]
     lib.pins_profile_read.argtypes = [P, P, P, I, I]
+    lib.pins_marginals_noalloc.argtypes = [ct.POINTER(pins_problem), D, I, D, P, P, P, P, P, P]
     for name in EXPORTED:
         if name not in ("pins_config_default", "pins_destroy", "pins_last_error"):
             getattr(lib, name).restype = ct.c_int
@@ -202,6 +203,12 @@ def pins_step_objective_increase(h, prob, s, F, G, df, dg, alpha, out) -> int:
 
 def pins_step_certificate(h, prob, s, F, G, out4) -> int:
     return load().pins_step_certificate(h, ct.byref(prob), s, _ptr(F), _ptr(G), _ptr(out4))
+
+
+def pins_marginals_noalloc(prob, eta, prec, s, F, G, r, c, out3, stream=None) -> int:
+    """Allocation-free marginal pass (see include/pins.h); queued on `stream`."""
+    return load().pins_marginals_noalloc(ct.byref(prob), eta, prec, s, _ptr(F), _ptr(G),
+                                         _ptr(r), _ptr(c), _ptr(out3), stream)
 
 
 def pins_profile_classes() -> int:
