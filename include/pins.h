@@ -225,7 +225,12 @@ pins_status pins_step_sparsify(pins_handle* h, const pins_problem* p, double s,
 /* Truncated Jacobi-preconditioned CG on M d = rhs with
  * M = (1/eta) [[diag r, S], [S^T, diag c]] (the negated sparsified Hessian of
  * Eq. eq:eppa-hess).  S is CSR (indptr m+1, indices/data nnz).  rhs, d: m + n
- * device doubles.  info (device, 2 doubles) = {iterations, relative residual}. */
+ * device doubles.  info (device, 2 doubles) = {iterations, relative residual}.
+ * On a PINS_PREC_FP64 handle every operation is FP64.  On a PINS_PREC_MIXED
+ * handle the vectors and the matrix-vector product are kept in double-float
+ * (FP32 pairs, ~48 significand bits) and the three inner products of each
+ * iteration are FP32 sums; the relative residual is then the FP32-measured
+ * ||r|| / ||rhs||. */
 pins_status pins_step_cg(pins_handle* h, int m, int n, double eta,
                          const double* r, const double* c, const int* indptr,
                          const int* indices, const double* data, int nnz,

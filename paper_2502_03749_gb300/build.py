@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include")]
 
-SOURCES = ["pins_kernels_f64.cu", "pins_kernels_mixed.cu", "pins_sparse.cu", "pins_select.cu", "pins_cg.cu",
+SOURCES = ["pins_kernels_f64.cu", "pins_kernels_mixed.cu", "pins_sparse.cu", "pins_select.cu", "pins_cg.cu", "pins_cg_dd.cu",
            "pins_noalloc.cu",
            "pins_solver.cu", "pins_api.cu"]
 

@@ -427,7 +427,8 @@ extern "C" pins_status pins_step_cg(pins_handle* h, int m, int n, double eta, co
   if (!h || !r || !c || !indptr || !rhs || !d || !info) return PINS_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
   return step_result(h, h->solver->step_cg(m, n, eta, r, c, indptr, indices, data, nnz, rhs, d,
-                                           rtol, max_iter, info));
+                                           rtol, max_iter, info,
+                                           h->cfg.prec == PINS_PREC_MIXED));
 }
 
 extern "C" pins_status pins_step_objective_increase(pins_handle* h, const pins_problem* p,

@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(PINS_CGC_TPB) k_pcg_cg1(CGClusterArgs a) {
     if (e < Kc) { v = __ldg(a.data + e); return a.m + __ldg(a.indices + e); }
     v = __ldg(a.cdata + e - Kc); return __ldg(a.rowidx + e - Kc);
   };
-  const int E0 = beg(lo), E1 = beg(lo + nl);
+  const int E0 = beg(min(lo, N)), E1 = beg(min(lo + nl, N));
   const int c0 = E0 + (int)(((long long)tid * (E1 - E0)) / PINS_CGC_TPB);
   const int c1 = E0 + (int)(((long long)(tid + 1) * (E1 - E0)) / PINS_CGC_TPB);
   int t0 = lo;                                      // unknown holding entry c0

@@ -1,0 +1,426 @@
+// Truncated Jacobi-preconditioned CG of the Newton step (Algorithm 2) for the
+// mixed-precision path: one thread-block cluster, every vector resident in
+// shared memory, all vector arithmetic in double-float (FP32 pairs).
+//
+// Why double-float: this GPU issues FP64 at ~1/70 of its FP32 rate, and a CG
+// iteration on a few thousand unknowns is a chain of short dependent steps, so
+// FP64 latency sets its length.  The recurrences that carry the solution keep
+// ~48 significand bits:
+//   x, r, p, s (double-float), w = M u (double-float SpMV, diagonal and S
+//   entries scaled by 1/eta in double-float),
+// while two things that only steer the iteration run in FP32:
+//   u = D^-1 r rounded to FP32 (a fixed diagonal preconditioner applied with
+//   relative error 2^-24; w is computed exactly from this u, so s = M p and
+//   r = rhs - M x hold to double-float accuracy), and the three inner products
+//   (r.u, w.u, r.r), whose FP32 rounding perturbs the step lengths alpha, beta
+//   by ~1e-6 relatively and so changes the rate, not the fixed point.
+// rhs is scaled by a power of two (exact) so that its largest entry is in
+// [1, 2); x is scaled back at the end.
+//
+// Ordering: the single-reduction PCG of Chronopoulos & Gear (J. Comput. Appl.
+// Math. 25, 1989), as in the FP64 cluster kernel: per iteration
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
+//   [cluster barrier]  w = M u,  (r.u, w.u, r.r)  [cluster barrier]
+//   beta = g'/g, alpha = g'/(d' - beta g'/alpha).
+// Every CTA sums the 16 block partials in the same order and takes the same
+// decisions, so results are reproducible run to run.
+#include <cooperative_groups.h>
+#include "pins_kernels.h"
+#include "pins_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pins {
+
+#define PINS_DDCG_MAX 16
+#define PINS_DDCG_TPB 256
+#define PINS_DDCG_SMEM (200 * 1024)
+// shared bytes per unknown: u (4) + r, x, p, s, w, diag, od (7 x 8) + D^-1 (4) + row begin (4)
+#define PINS_DDCG_PER_UNKNOWN 68
+
+struct CGddArgs {
+  int m, n;
+  double inv_eta;
+  const double* r; const double* c;
+  const int* indptr; const int* indices; const double* data;
+  const int* colptr; const int* rowidx; const double* cdata;
+  const double* rhs; double* x;
+  int* ent_tgt; float2* ent_val;   // scratch: one slot per entry of the CSR + CSC entry space
+  float rtol2; int max_iter; double* info;
+  int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
+};
+
+// FP64 -> double-float with integer operations only: hi = the sign, exponent and
+// top 23 stored significand bits (truncated), lo = the remaining 29 bits rounded
+// to FP32, so hi + lo carries ~48 significand bits.  The binary exponent is
+// lowered by `shift` (an exact scaling by 2^-shift).  Zero, FP64 subnormals and
+// scaled magnitudes below 2^-126 give 0; above 2^128 give inf; NaN stays NaN.
+__device__ __forceinline__ float2 split_f64(double v, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.f);
+  const int fe = e - 1023 + 127 - shift;
+  if (e == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
+  const unsigned rest = (unsigned)(mant & 0x1fffffffu);
+  // rest * 2^-52 is exact and normal; times 2^(fe - 127) may round if subnormal
+  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(rest), 0x1p-52f), __uint_as_float((unsigned)fe << 23));
+  if (sign) lo = -lo;
+  return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ float2 ddv_mul(float2 a, float2 b) {
+  float p, e; two_prod(a.x, b.x, p, e);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float h, l; fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+// y + f * v  (f FP32, v and y double-float), normalised
+__device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
+  float p, e; two_prod(f, v.x, p, e);
+  e = __fmaf_rn(f, v.y, e);
+  float s, t; two_sum(y.x, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(y.y, e));
+  float h, l; fast_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
+// acc += v * u (v double-float, u FP32), unnormalised accumulation
+__device__ __forceinline__ void ddv_acc_mul(float2& acc, float2 v, float u) {
+  float p, e; two_prod(v.x, u, p, e);
+  e = __fmaf_rn(v.y, u, e);
+  float s, t; two_sum(acc.x, p, s, t);
+  acc.x = s; acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+}
+__device__ __forceinline__ float2 ddv_add(float2 a, float2 b) {
+  float s, t; two_sum(a.x, b.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+  float h, l; fast_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
+
+__global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char ddcg_smem[];
+  __shared__ float* rem_u[PINS_DDCG_MAX];
+  __shared__ float slot[3 * PINS_DDCG_MAX];
+  __shared__ unsigned int eslot[1];
+  __shared__ float red[3][PINS_DDCG_TPB / 32];
+  __shared__ unsigned int ered[PINS_DDCG_TPB / 32];
+  __shared__ int hrow[PINS_DDCG_TPB];
+  __shared__ float2 hval[PINS_DDCG_TPB];
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = a.m, N = a.m + a.n;
+  const int L = (N + CS - 1) / CS;
+  const int lo = rank * L;
+  const int nl = max(0, min(N, lo + L) - lo);
+  float2* rv = reinterpret_cast<float2*>(ddcg_smem);
+  float2* xv = rv + L;
+  float2* pv = xv + L;
+  float2* sv = pv + L;
+  float2* wv = sv + L;
+  float2* dg = wv + L;        // diag / eta
+  float2* od = dg + L;        // off-diagonal part of M u (zeroed after use)
+  float* u = reinterpret_cast<float*>(od + L);   // read by other CTAs
+  float* dinv = u + L;
+  int* rb = reinterpret_cast<int*>(dinv + L);    // L + 1 entry offsets (relative to E0)
+  if (tid < CS) rem_u[tid] = cluster.map_shared_rank(u, tid);
+
+  const int Kc = __ldg(a.indptr + m);
+  auto beg = [&](int t) -> int {
+    return (t < m) ? __ldg(a.indptr + t) : Kc + __ldg(a.colptr + t - m);
+  };
+  const float2 ie = split_f64(a.inv_eta, 0);
+
+  // ---- scale: largest binary exponent of rhs over the cluster ----
+  unsigned int emax = 0u;
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a.rhs[lo + k]);
+    emax = max(emax, (unsigned)((b >> 52) & 0x7ffu));
+  }
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if (lane == 0) ered[warp] = emax;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int v = lane < PINS_DDCG_TPB / 32 ? ered[lane] : 0u;
+    v = __reduce_max_sync(0xffffffffu, v);
+    if (lane == 0) eslot[0] = v;                    // read by the other CTAs after the barrier
+  }
+  // ---- own unknowns: diagonal, preconditioner, residual, row offsets ----
+  const int E0 = beg(min(lo, N));
+  const int E1 = beg(min(lo + nl, N));
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    const int t = lo + k;
+    const double d = (t < m) ? __ldg(a.r + t) : __ldg(a.c + t - m);
+    const float2 dd_ = ddv_mul(split_f64(d, 0), ie);
+    dg[k] = dd_;
+    dinv[k] = __frcp_rn(dd_.x);
+    xv[k] = make_float2(0.f, 0.f);
+    pv[k] = make_float2(0.f, 0.f);
+    sv[k] = make_float2(0.f, 0.f);
+    od[k] = make_float2(0.f, 0.f);
+    rb[k] = beg(t) - E0;
+  }
+  if (tid == 0) rb[nl] = E1 - E0;
+  // ---- entries of the own unknowns: packed (owner, offset) and value / eta ----
+  for (int e = E0 + tid; e < E1; e += PINS_DDCG_TPB) {
+    int g; double v;
+    if (e < Kc) { v = __ldg(a.data + e); g = m + __ldg(a.indices + e); }
+    else { v = __ldg(a.cdata + e - Kc); g = __ldg(a.rowidx + e - Kc); }
+    int ow = g / L, off = g - ow * L;
+    float2 val = ddv_mul(split_f64(v, 0), ie);
+    if (g < 0 || g >= N || ow >= CS || off >= L) {
+      atomicOr(a.flag, 1);
+      ow = rank; off = 0; val = make_float2(0.f, 0.f);
+    }
+    a.ent_tgt[e] = (ow << 16) | off;
+    a.ent_val[e] = val;
+  }
+  // first cluster barrier: every CTA has started (no distributed shared memory
+  // access precedes it) and has published its block maximum
+  cluster.sync();
+  unsigned int E = 0u;
+  for (int q = 0; q < CS; ++q) E = max(E, *cluster.map_shared_rank(eslot, q));
+  const int shift = (int)E - 1023;                  // max |rhs| 2^-shift in [1, 2)
+  float lr = 0.f;
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    const float2 r0 = split_f64(a.rhs[lo + k], shift);
+    rv[k] = r0;
+    u[k] = __fmul_rn(dinv[k], r0.x);
+  }
+  // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
+  const int ne = E1 - E0;
+  const int c0 = (int)(((long long)tid * ne) / PINS_DDCG_TPB);
+  const int c1 = (int)(((long long)(tid + 1) * ne) / PINS_DDCG_TPB);
+  __syncthreads();                                  // rb[], entries visible in the block
+  int t0 = 0;                                       // last local unknown with rb <= c0
+  if (c0 < c1) {
+    int lo_s = 0, hi_s = nl - 1;
+    while (lo_s < hi_s) {
+      const int mid = (lo_s + hi_s + 1) >> 1;
+      if (rb[mid] <= c0) lo_s = mid; else hi_s = mid - 1;
+    }
+    t0 = lo_s;
+  }
+  const bool starts_mid = (c0 < c1) && rb[t0] < c0;
+  // written above by this CTA: plain (coherent) loads, not the read-only path
+  const int* etg = a.ent_tgt + E0;
+  const float2* eva = a.ent_val + E0;
+
+  // od[t] = sum over the row/column entries of (S/eta) u, for the own unknowns
+  auto spmv = [&]() {
+    int t = t0;
+    bool first = true;
+    float2 acc = make_float2(0.f, 0.f);
+    float2 headv = make_float2(0.f, 0.f), tailv = make_float2(0.f, 0.f);
+    int headrow = -1, tailrow = -1;
+    auto close_row = [&](bool ended_inside) {
+      if (first && starts_mid) { headrow = t; headv = acc; }
+      else if (!ended_inside) { tailrow = t; tailv = acc; }
+      else od[t] = acc;
+      first = false;
+      acc = make_float2(0.f, 0.f);
+    };
+    for (int base = c0; base < c1; base += 4) {
+      int tg[4]; float2 v[4]; float uu[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = base + q;
+        tg[q] = (e < c1) ? etg[e] : (rank << 16);
+        v[q] = (e < c1) ? eva[e] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) uu[q] = rem_u[tg[q] >> 16][tg[q] & 0xffff];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = base + q;
+        if (e < c1) {
+          while (rb[t + 1] <= e) { close_row(true); ++t; }
+          ddv_acc_mul(acc, v[q], uu[q]);
+        }
+      }
+    }
+    if (c0 < c1) close_row(rb[t + 1] <= c1);
+    hrow[tid] = (c0 < c1) ? headrow : -2;           // -2: empty slice, skipped below
+    hval[tid] = headv;
+    __syncthreads();
+    if (tailrow >= 0) {
+      float2 s = tailv;
+      for (int k = tid + 1; k < PINS_DDCG_TPB; ++k) {
+        if (hrow[k] == -2) continue;
+        if (hrow[k] != tailrow) break;
+        s = ddv_add(s, hval[k]);
+      }
+      od[tailrow] = s;
+    }
+    __syncthreads();
+  };
+  // three block partials -> every CTA's slots -> cluster barrier -> every warp
+  // sums the slots in the same butterfly order (bit-identical in all lanes/CTAs)
+  auto reduce3 = [&](float v0, float v1, float v2, float& t0r, float& t1r, float& t2r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+    }
+    if (lane == 0) { red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; }
+    __syncthreads();
+    if (warp == 0) {
+      constexpr int W = PINS_DDCG_TPB / 32;
+      float b0 = lane < W ? red[0][lane] : 0.f;
+      float b1 = lane < W ? red[1][lane] : 0.f;
+      float b2 = lane < W ? red[2][lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+      }
+      if (lane < CS) {
+        float* rs = cluster.map_shared_rank(slot, lane);
+        rs[0 * PINS_DDCG_MAX + rank] = b0;
+        rs[1 * PINS_DDCG_MAX + rank] = b1;
+        rs[2 * PINS_DDCG_MAX + rank] = b2;
+      }
+    }
+    cluster.sync();
+    float q0 = lane < CS ? slot[0 * PINS_DDCG_MAX + lane] : 0.f;
+    float q1 = lane < CS ? slot[1 * PINS_DDCG_MAX + lane] : 0.f;
+    float q2 = lane < CS ? slot[2 * PINS_DDCG_MAX + lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+      q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+      q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+    }
+    t0r = q0; t1r = q1; t2r = q2;
+  };
+  // w = diag u + od, od reset; partial inner products
+  auto apply_w = [&](float& lg, float& ld, float& lrr) {
+    lg = 0.f; ld = 0.f; lrr = 0.f;
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float uk = u[k];
+      float2 w = od[k];
+      ddv_acc_mul(w, dg[k], uk);
+      float h, l; fast_two_sum(w.x, w.y, h, l);
+      w = make_float2(h, l);
+      wv[k] = w;
+      od[k] = make_float2(0.f, 0.f);
+      const float rk = rv[k].x;
+      lg = __fmaf_rn(rk, uk, lg);
+      ld = __fmaf_rn(w.x, uk, ld);
+      lrr = __fmaf_rn(rk, rk, lrr);
+    }
+  };
+
+  cluster.sync();                                   // every u slice ready
+  spmv();
+  float lg, ld;
+  apply_w(lg, ld, lr);
+  float gam, dlt, bb;
+  reduce3(lg, ld, lr, gam, dlt, bb);
+  float alpha = (dlt != 0.f) ? gam / dlt : 0.f;
+  float beta = 0.f;
+  float rr = bb;
+  int it = 0;
+  bool stop = !(bb > 0.f);
+  while (!stop && it < a.max_iter) {
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float uk = u[k];
+      float2 p = ddv_axpy(beta, pv[k], make_float2(uk, 0.f));
+      float2 s = ddv_axpy(beta, sv[k], wv[k]);
+      pv[k] = p; sv[k] = s;
+      xv[k] = ddv_axpy(alpha, p, xv[k]);
+      const float2 r1 = ddv_axpy(-alpha, s, rv[k]);
+      rv[k] = r1;
+      u[k] = __fmul_rn(dinv[k], r1.x);
+    }
+    ++it;
+    cluster.sync();                                 // every u slice updated
+    spmv();
+    apply_w(lg, ld, lr);
+    float gn, dn;
+    reduce3(lg, ld, lr, gn, dn, rr);
+    stop = !(rr > a.rtol2 * bb);                    // ||r|| <= rtol ||rhs|| (NaN stops)
+    if (stop) break;
+    beta = gn / gam;
+    alpha = gn / (dn - beta * gn / alpha);
+    gam = gn;
+  }
+  const double scale = ldexp(1.0, shift);
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB)
+    a.x[lo + k] = ((double)xv[k].x + (double)xv[k].y) * scale;
+  if (rank == 0 && tid == 0) {
+    a.info[0] = (double)it;
+    a.info[1] = (bb > 0.f) ? sqrt((double)rr / (double)bb) : 0.0;
+  }
+  cluster.sync();                                   // no CTA exits while others read its u
+}
+
+static int ddcg_cluster_size() {
+  static int cs = 0;
+  if (cs) return cs;
+  cudaFuncSetAttribute(k_pcg_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
+  cs = 8;
+  if (cudaFuncSetAttribute(k_pcg_dd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+      cudaSuccess) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(16);
+    lc.blockDim = dim3(PINS_DDCG_TPB);
+    lc.dynamicSmemBytes = PINS_DDCG_SMEM;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr; lc.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_dd, &lc) == cudaSuccess && nclusters >= 1)
+      cs = 16;
+  }
+  cudaGetLastError();
+  return cs;
+}
+
+size_t ddcg_smem_bytes(int N, int cs) {
+  const int L = (N + cs - 1) / cs;
+  return (size_t)PINS_DDCG_PER_UNKNOWN * L + 16;
+}
+
+cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
+                          const int* indptr, const int* indices, const double* data,
+                          const int* colptr, const int* rowidx, const double* cdata,
+                          const double* rhs, double* x, int* ent_tgt, float2* ent_val,
+                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
+                          bool* used) {
+  *used = false;
+  const int N = m + n;
+  const int CS = ddcg_cluster_size();
+  const int L = (N + CS - 1) / CS;
+  const size_t smem = ddcg_smem_bytes(N, CS);
+  if (smem > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
+  CGddArgs a;
+  a.m = m; a.n = n; a.inv_eta = 1.0 / eta;
+  a.r = r; a.c = c; a.indptr = indptr; a.indices = indices; a.data = data;
+  a.colptr = colptr; a.rowidx = rowidx; a.cdata = cdata;
+  a.rhs = rhs; a.x = x; a.ent_tgt = ent_tgt; a.ent_val = ent_val;
+  a.rtol2 = (float)(rtol * rtol); a.max_iter = max_iter; a.info = info; a.flag = flag;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(CS);
+  lc.blockDim = dim3(PINS_DDCG_TPB);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  *used = true;
+  return cudaLaunchKernelEx(&lc, k_pcg_dd, a);
+}
+
+}  // namespace pins

@@ -57,6 +57,14 @@ cudaError_t launch_pcg_cluster(int m, int n, double eta, const double* r, const 
                                const int* colptr, const int* rowidx, const double* cdata,
                                const double* rhs, double* x, double rtol, int max_iter,
                                double* info, int* flag, cudaStream_t st, bool* used);
+// Double-float CG of the mixed path (one cluster); *used = false when the
+// problem does not fit, and then nothing was launched.
+cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
+                          const int* indptr, const int* indices, const double* data,
+                          const int* colptr, const int* rowidx, const double* cdata,
+                          const double* rhs, double* x, int* ent_tgt, float2* ent_val,
+                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
+                          bool* used);
 void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
 void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,

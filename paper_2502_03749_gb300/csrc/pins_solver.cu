@@ -94,6 +94,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.sw.data = cv.take<double>(kcap);
   w.sw.colptr = cv.take<int>(n + 1); w.sw.rowidx = cv.take<int>(kcap);
   w.sw.cdata = cv.take<double>(kcap);
+  w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
   w.cg_part = cv.take<double>(3 * 64 + 8);
   w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
   w.a = ip.ab ? cv.take<double>(m) : nullptr;
@@ -569,11 +570,9 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
       cudaMemsetAsync(ws_.cg_part + 3 * 64, 0, sizeof(double), stream_);   // CG index-check flag
       prof_begin(PC_CG);
-      cudaError_t ce = launch_pcg(m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
-                                  ws_.sw.data, ws_.sw.colptr, ws_.sw.rowidx, ws_.sw.cdata,
-                                  ws_.grad, ws_.dir, ws_.cg_res, ws_.cg_p, ws_.cg_q,
-                                  ws_.cg_part, cfg.cg_rtol, max_cg, ws_.scal + SC_CG, sms_,
-                                  stream_);
+      cudaError_t ce = run_cg(mixed_, m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
+                              ws_.sw.data, ws_.grad, ws_.dir, cfg.cg_rtol, max_cg,
+                              ws_.scal + SC_CG);
       prof_end();
       if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
       launch_dot2(ws_.grad, ws_.dir, ws_.ab, ws_.dir, m + n, ws_.scal + SC_DOTS, stream_);
@@ -729,18 +728,35 @@ pins_status Solver::step_sparsify(const pins_config& cfg, const pins_problem& p,
   return sync("step_sparsify");
 }
 
+cudaError_t Solver::run_cg(bool mixed, int m, int n, double eta, const double* r,
+                           const double* c, const int* indptr, const int* indices,
+                           const double* data, const double* rhs, double* d, double rtol,
+                           int max_iter, double* info) {
+  if (mixed) {
+    bool used = false;
+    cudaError_t ce = launch_pcg_dd(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
+                                   ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.ent_tgt, ws_.ent_val,
+                                   rtol, max_iter, info,
+                                   reinterpret_cast<int*>(ws_.cg_part + 3 * 64), stream_, &used);
+    if (used) return ce;
+  }
+  return launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr, ws_.sw.rowidx,
+                    ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p, ws_.cg_q, ws_.cg_part, rtol,
+                    max_iter, info, sms_, stream_);
+}
+
 pins_status Solver::step_cg(int m, int n, double eta, const double* r, const double* c,
                             const int* indptr, const int* indices, const double* data, int nnz,
                             const double* rhs, double* d, double rtol, int max_iter,
-                            double* info) {
+                            double* info, bool mixed) {
   err_.clear();
   if (m < 1 || n < 1 || nnz < 0 || !(eta > 0.0) || max_iter < 0) { err_ = "bad CG arguments"; return PINS_ERR_INVALID_ARG; }
   pins_status st = ensure(m, n, std::max(nnz, 1), 1, PINS_COST_GRID_SQEUCLID, false, false, 1);
   if (st != PINS_OK) return st;
   build_csc_from_csr(indptr, indices, data, m, n, nnz, ws_.sw, stream_);
-  cudaError_t ce = launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
-                              ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p,
-                              ws_.cg_q, ws_.cg_part, rtol, max_iter, info, sms_, stream_);
+  cudaMemsetAsync(ws_.cg_part + 3 * 64, 0, sizeof(double), stream_);   // index-check flag
+  cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, rhs, d, rtol,
+                          max_iter, info);
   launches_ += 5;
   if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); return PINS_ERR_CUDA; }
   return sync("step_cg");

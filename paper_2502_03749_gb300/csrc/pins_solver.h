@@ -24,6 +24,7 @@ struct Workspace {
   unsigned int* hist;
   double* cand_key; long long* cand_idx;
   SparseWS sw;
+  int* ent_tgt; float2* ent_val;   // double-float CG: packed entries (2 kcap)
   double* cg_part;
   double* scal;            // device scalars (see Solver::SC_*)
   // uploaded inputs
@@ -65,7 +66,8 @@ class Solver {
                             int* indices, double* data);
   pins_status step_cg(int m, int n, double eta, const double* r, const double* c,
                       const int* indptr, const int* indices, const double* data, int nnz,
-                      const double* rhs, double* d, double rtol, int max_iter, double* info);
+                      const double* rhs, double* d, double rtol, int max_iter, double* info,
+                      bool mixed);
   pins_status step_objective_increase(const pins_config& cfg, const pins_problem& p, double s,
                                       const double* F, const double* G, const double* df,
                                       const double* dg, double alpha, double* out);
@@ -73,6 +75,11 @@ class Solver {
                                const double* F, const double* G, double* out4);
 
   const std::string& error() const { return err_; }
+  // the CG of one Newton step (double-float cluster kernel on the mixed path when
+  // it fits, else the FP64 kernels)
+  cudaError_t run_cg(bool mixed, int m, int n, double eta, const double* r, const double* c,
+                     const int* indptr, const int* indices, const double* data,
+                     const double* rhs, double* d, double rtol, int max_iter, double* info);
   long long launches() const { return launches_; }
 
   // Optional per-kernel-class device timing: CUDA events recorded on the

@@ -207,3 +207,54 @@ def test_step_rejects_host_pointers(handles):
     G = torch.zeros(5, dtype=torch.float64, device="cuda")
     assert pins.pins_step_sinkhorn(handles["fp64"].h, pr.prob, 1.0, 1, F, G, None) == \
         pins.PINS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("m,n,rtol", [(70, 150, 1e-10), (40, 40, 1e-10), (1, 9, 1e-10),
+                                      (700, 1500, 1e-6), (1234, 777, 1e-9)])
+def test_cg_double_float_matches_dense_solve(handles, m, n, rtol):
+    """The mixed handle runs the CG in double-float arithmetic with FP32 inner
+    products: M d must still reproduce rhs to the requested relative residual,
+    and the iteration count stays close to the FP64 oracle's."""
+    import torch
+    C, a, b, F, G, eta, s = random_state(m, n, 7 * m + n)
+    ga, gb, r, c = po.gradient(C, a, b, F, G, eta, s)
+    S = po.sparsify(C, F, G, eta, s, min(m * n, m + n - 1))
+    rhs = np.concatenate([ga, gb])
+    d = torch.zeros(m + n, dtype=torch.float64, device="cuda")
+    info = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_cg(handles["mixed"].h, m, n, eta, dev(r), dev(c),
+                           dev(S.indptr.astype(np.int32)), dev(S.indices.astype(np.int32)),
+                           dev(S.data), S.nnz, dev(rhs), d, rtol, 5000, info)
+    assert st == 0, handles["mixed"].error()
+    it, rel = info.cpu().numpy()
+    assert rel <= rtol * 1.0001
+    dd_ = d.cpu().numpy()
+    Sd = S.dense()
+    M = np.block([[np.diag(r), Sd], [Sd.T, np.diag(c)]]) / eta
+    true_rel = np.linalg.norm(M @ dd_ - rhs) / np.linalg.norm(rhs)
+    assert true_rel <= 2.0 * rtol + 1e-12
+    if S.nnz < m * n and m + n <= 1500:
+        want = np.linalg.solve(M, rhs)
+        err = np.linalg.norm(dd_ - want) / np.linalg.norm(want)
+        assert err <= max(1e-6, 1e4 * rtol)
+    dfo, dgo, ito, _ = po.pcg(r, c, S, eta, ga, gb, rtol=rtol, max_iter=5000)
+    assert abs(int(it) - ito) <= max(3, ito // 5)
+
+
+def test_cg_double_float_is_deterministic(handles):
+    import torch
+    m, n = 300, 500
+    C, a, b, F, G, eta, s = random_state(m, n, 11)
+    ga, gb, r, c = po.gradient(C, a, b, F, G, eta, s)
+    S = po.sparsify(C, F, G, eta, s, m + n - 1)
+    rhs = np.concatenate([ga, gb])
+    outs = []
+    for _ in range(3):
+        d = torch.zeros(m + n, dtype=torch.float64, device="cuda")
+        info = torch.zeros(2, dtype=torch.float64, device="cuda")
+        st = pins.pins_step_cg(handles["mixed"].h, m, n, eta, dev(r), dev(c),
+                               dev(S.indptr.astype(np.int32)), dev(S.indices.astype(np.int32)),
+                               dev(S.data), S.nnz, dev(rhs), d, 1e-8, 5000, info)
+        assert st == 0
+        outs.append(d.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
