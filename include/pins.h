@@ -239,7 +239,11 @@ pins_status pins_step_cg(pins_handle* h, int m, int n, double eta,
 
 /* Objective increase for the Armijo test (Algorithm 2 line search):
  * out (device, 1 double) = P(x + alpha d) - P(x) = alpha (<a,df> + <b,dg>)
- *   - eta sum_ij X~_ij expm1(alpha (df_i + dg_j) / eta);  -inf on overflow. */
+ *   - eta sum_ij X~_ij expm1(alpha (df_i + dg_j) / eta);  -inf on overflow.
+ * A PINS_PREC_MIXED handle evaluates the equal form alpha (<a - r, df> +
+ * <b - c, dg>) - eta sum_ij X~_ij (expm1(t_ij) - t_ij), t_ij = alpha (df_i +
+ * dg_j) / eta, with r, c the marginals of X~: its terms do not cancel, so the
+ * nonnegative sum is taken in FP32. */
 pins_status pins_step_objective_increase(pins_handle* h, const pins_problem* p,
                                          double s, const double* F,
                                          const double* G, const double* df,

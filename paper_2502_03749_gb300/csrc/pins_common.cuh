@@ -25,6 +25,7 @@
 #define PINS_GX_MAX 32        // column-strip CTAs (row partial fan-in)
 #define PINS_GY_MAX 64        // row-block CTAs (column partial fan-in)
 #define PINS_EXP_TABLE 1024   // entries of the 2^(k/1024) table
+#define PINS_ROW_GROUPS 256   // arrival counters for row groups (cnt_row)
 
 namespace pins {
 
@@ -113,6 +114,25 @@ __device__ __forceinline__ dd dd_exp(float zh, float zl, const float2* __restric
   out.hi = sh * fa * fb;
   out.lo = sl * fa * fb;
   return out;
+}
+
+// expm1(y) - y in FP32 with small relative error for every y: Taylor series
+// y^2 (1/2! + y/3! + ... + y^8/10!) for |y| < 1/2 (remainder below 1e-10
+// relative), expf(y) - 1 - y beyond (relative error below ~1e-6).
+__device__ __forceinline__ float expm1_minus_x(float y) {
+  if (fabsf(y) < 0.5f) {
+    float p = 1.0f / 3628800.0f;
+    p = __fmaf_rn(p, y, 1.0f / 362880.0f);
+    p = __fmaf_rn(p, y, 1.0f / 40320.0f);
+    p = __fmaf_rn(p, y, 1.0f / 5040.0f);
+    p = __fmaf_rn(p, y, 1.0f / 720.0f);
+    p = __fmaf_rn(p, y, 1.0f / 120.0f);
+    p = __fmaf_rn(p, y, 1.0f / 24.0f);
+    p = __fmaf_rn(p, y, 1.0f / 6.0f);
+    p = __fmaf_rn(p, y, 0.5f);
+    return __fmul_rn(__fmul_rn(y, y), p);
+  }
+  return __fsub_rn(__fsub_rn(expf(y), 1.0f), y);
 }
 
 // expm1 of a double-float argument with relative accuracy ~2^-44 for small |t|.
@@ -304,7 +324,7 @@ __host__ __device__ inline TileGeom make_geom(int m, int n) {
 
 // Cross-CTA merge bookkeeping (deterministic "last block" pattern).
 struct MergeWS {
-  unsigned int* cnt_row;   // gy counters (arrivals of gx strips)
+  unsigned int* cnt_row;   // PINS_ROW_GROUPS counters (arrivals of the strips of a row group)
   unsigned int* cnt_col;   // gx counters (arrivals of gy row blocks)
   unsigned int* cnt_all;   // 1 counter (arrivals of gx*gy CTAs)
   double* rowpart0;        // gx * m

@@ -31,14 +31,13 @@ struct PassSet {
 const PassSet* passes_f64(int kind);
 const PassSet* passes_mixed(int kind);
 
-#define PINS_CSC_CHUNKS 256
 
 // sparse/vector launchers (pins_sparse.cu, pins_select.cu)
 struct SparseWS {
   int* rowcnt; int* colcnt;     // m, n
   int* indptr; int* indices; double* data;    // CSR: m+1, cap, cap
   int* colptr; int* rowidx; double* cdata;    // CSC: n+1, cap, cap
-  int* chunkcnt;                // PINS_CSC_CHUNKS * n
+  int* trow; double* tval;       // CSC placement before the per-column sort: cap, cap
 };
 void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
                         int nnz, const SparseWS& sw, cudaStream_t st);

@@ -2,18 +2,59 @@
 // Included once per policy translation unit with PINS_POLICY and PINS_PASSES_FN set.
 #include "pins_sparsify.cuh"
 #include "pins_kernels.h"
+#include <algorithm>
 
 namespace pins {
 namespace {
+
+int sm_count() {
+  static int v = 0;
+  if (!v) {
+    int d = 0;
+    cudaGetDevice(&d);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
+      v = 148;
+  }
+  return v;
+}
+
+#define PINS_ROW_SEG_SMEM (96 * 1024)
 
 template <int K> struct Launch {
   using P = PINS_POLICY<K>;
   static void row_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* F_out,
                       double* out_res, cudaStream_t st) {
+    if constexpr (P::MIXED) {
+      // column segments of ~1024 (at most g.gx of them: rowpart0 holds g.gx * m),
+      // row groups for ~4 CTAs per SM (at most PINS_ROW_GROUPS counters)
+      const int sx = std::max(1, std::min(g.gx, (p.n + 1023) / 1024));
+      const int seg = (((p.n + sx - 1) / sx) + PINS_TC - 1) / PINS_TC * PINS_TC;
+      const size_t smem = sizeof(float2) * (size_t)seg;
+      if (smem <= PINS_ROW_SEG_SMEM) {
+        static bool configured = false;
+        if (!configured) {
+          cudaFuncSetAttribute(k_row_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               PINS_ROW_SEG_SMEM);
+          configured = true;
+        }
+        const int gy = std::max(1, std::min({(4 * sm_count() + sx - 1) / sx, PINS_ROW_GROUPS,
+                                             (p.m + PINS_WARPS - 1) / PINS_WARPS}));
+        k_row_lse_mx<P><<<dim3(sx, gy), PINS_TPB, smem, st>>>(p, seg, ws, F_out, out_res);
+        return;
+      }
+    }
     k_row_lse<P><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, F_out, out_res);
   }
   static void col_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* G_out,
                       cudaStream_t st) {
+    if constexpr (P::MIXED) {
+      // row blocks for ~4 CTAs per SM, at most g.gy (colpart0 holds g.gy * n)
+      const int gy = std::max(1, std::min({(4 * sm_count() + g.gx - 1) / g.gx, g.gy,
+                                           (p.m + PINS_WARPS - 1) / PINS_WARPS}));
+      const int rb = (p.m + gy - 1) / gy;
+      k_col_lse_mx<P><<<dim3(g.gx, gy), PINS_TPB, 0, st>>>(p, rb, ws, G_out);
+      return;
+    }
     k_col_lse<P><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, G_out);
   }
   static void marg(const PassArgs& p, const TileGeom& g, const MergeWS& ws, const TrialArgs* tr,

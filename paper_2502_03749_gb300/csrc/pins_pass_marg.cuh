@@ -2,8 +2,15 @@
 // pass (Algorithm 2 LineSearch, reading R7).  Per entry e = X~_ij = exp(z_ij).
 //   TRIAL = false: r_i = sum_j e, c_j = sum_i e.
 //   TRIAL = true : t_ij = Pt_i + Qt_j (= alpha (df_i + dg_j) / eta),
-//                  e' = e (1 + expm1 t): r_i = sum_j e', c_j = sum_i e',
-//                  d_i = sum_j e expm1(t)  (objective increase term).
+//                  e' = exp(z + t): r_i = sum_j e', c_j = sum_i e', and the
+//                  objective increase term d_i:
+//                  FP64 policy  d_i = sum_j e expm1(t)          (as the oracle)
+//                  mixed policy d_i = sum_j e (expm1(t) - t)    (FP32, >= 0)
+//   The two give the same increase: P(x + alpha d) - P(x)
+//     = alpha (<a,df> + <b,dg>) - eta sum e expm1(t)
+//     = alpha (<a - r, df> + <b - c, dg>) - eta sum e (expm1(t) - t),
+//   since sum_ij e t_ij = (alpha / eta)(<r, df> + <c, dg>).  The second form has
+//   no cancellation between its terms, so FP32 is enough for the sum.
 // Scalars (out[]): 0 residual ||r - a||_1 + ||c - b||_1, 1 sum X (of e or e'),
 //                  2 max_ij z (of e or e'), 3 sum_i d_i (TRIAL).
 #pragma once
@@ -85,24 +92,25 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
           const float2 A = P::row(p, i);
           const float2 Pt = TRIAL ? tr.Ptdd[i] : make_float2(0.f, 0.f);
           dd racc; racc.hi = 0.f; racc.lo = 0.f;
-          dd dacc; dacc.hi = 0.f; dacc.lo = 0.f;
+          float dfs = 0.f;
 #pragma unroll
           for (int q = 0; q < PINS_CPL; ++q) {
             if (jj[q] >= n) continue;
             float wh, wl, zh, zl;
             dd_w(cd[q], P::cost(p, i, jj[q]), kh, kl, wh, wl);
             dd_z(A, wh, wl, zh, zl);
-            dd e = dd_exp(zh, zl, s_tab);
             if constexpr (TRIAL) {
               float th, tl; two_sum(Pt.x, Qf[q].x, th, tl);
               tl = __fadd_rn(tl, __fadd_rn(Pt.y, Qf[q].y));
-              const dd em1 = dd_expm1(th, tl, s_tab);
-              const dd de = dd_mul(e, em1);
-              dd_acc(dacc, de.hi, de.lo);
-              e = dd_add(e, de);
-              zh = zh + th;
-              zl = zl + tl;
+              // objective term X~ (expm1(t) - t) >= 0: FP32 suffices (no cancellation)
+              const float ef = exp2f(__fadd_rn(zh, zl) * 1.4426950408889634f);
+              dfs = __fmaf_rn(ef, expm1_minus_x(__fadd_rn(th, tl)), dfs);
+              // trial point z + t in double-float
+              float sh, se; two_sum(zh, th, sh, se);
+              se = __fadd_rn(se, __fadd_rn(zl, tl));
+              fast_two_sum(sh, se, zh, zl);
             }
+            const dd e = dd_exp(zh, zl, s_tab);
             // the FP32 value of z, as ranked by Sparsify (hi alone can be off by
             // |A| 2^-24 when A and B cancel)
             zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
@@ -111,6 +119,7 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
           }
           // row partial reduced across the warp in double-float, kept raw
           racc = warp_dd_sum(racc);
+          dd dacc; dacc.hi = dfs; dacc.lo = 0.f;
           if constexpr (TRIAL) dacc = warp_dd_sum(dacc);
           if (lane == 0) {
             if (!first) {

@@ -12,6 +12,7 @@
 // FP32 units (double-float pairs stored raw in the 8-byte partial slots) and
 // converts to FP64 once per row or column at the end of a merge.
 #pragma once
+#include <type_traits>
 #include "pins_common.cuh"
 
 namespace pins {
@@ -120,5 +121,6 @@ __device__ __forceinline__ float2 as_f2(double v) { return *reinterpret_cast<flo
 }  // namespace pins
 
 #include "pins_pass_lse.cuh"
+#include "pins_pass_lse_mx.cuh"
 #include "pins_pass_marg.cuh"
 #include "pins_pass_cert.cuh"

@@ -82,18 +82,18 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.mws.colpart1 = cv.take<double>((size_t)g.gy * n);
   w.mws.scal_row = cv.take<double>(8 * PINS_GY_MAX);
   w.mws.scal_col = cv.take<double>(4 * PINS_GX_MAX * PINS_GY_MAX + PINS_GX_MAX);
-  w.mws.cnt_row = cv.take<unsigned int>(PINS_GY_MAX);
+  w.mws.cnt_row = cv.take<unsigned int>(PINS_ROW_GROUPS);
   w.mws.cnt_col = cv.take<unsigned int>(PINS_GX_MAX);
   w.mws.cnt_all = cv.take<unsigned int>(1);
   w.st = cv.take<SparsifyState>(1);
   w.hist = cv.take<unsigned int>(PINS_HIST_NB + 1);
   w.cand_key = cv.take<double>(PINS_CAND_CAP); w.cand_idx = cv.take<long long>(PINS_CAND_CAP);
-  w.sw.chunkcnt = cv.take<int>((size_t)PINS_CSC_CHUNKS * n);
   w.sw.rowcnt = cv.take<int>(m); w.sw.colcnt = cv.take<int>(n);
   w.sw.indptr = cv.take<int>(m + 1); w.sw.indices = cv.take<int>(kcap);
   w.sw.data = cv.take<double>(kcap);
   w.sw.colptr = cv.take<int>(n + 1); w.sw.rowidx = cv.take<int>(kcap);
   w.sw.cdata = cv.take<double>(kcap);
+  w.sw.trow = cv.take<int>(kcap); w.sw.tval = cv.take<double>(kcap);
   w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
   w.cg_part = cv.take<double>(3 * 64 + 8);
   w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
@@ -225,10 +225,11 @@ pins_status Solver::ensure(int m, int n, int kcap, int t1cap, int kind, bool mix
   ws_.base = base; ws_.bytes = bytes;
   ws_.m = m; ws_.n = n; ws_.kcap = kcap; ws_.t1cap = t1cap;
   // counters start at zero; every kernel leaves them at zero
-  cudaMemsetAsync(ws_.mws.cnt_row, 0, sizeof(unsigned int) * PINS_GY_MAX, stream_);
+  cudaMemsetAsync(ws_.mws.cnt_row, 0, sizeof(unsigned int) * PINS_ROW_GROUPS, stream_);
   cudaMemsetAsync(ws_.mws.cnt_col, 0, sizeof(unsigned int) * PINS_GX_MAX, stream_);
   cudaMemsetAsync(ws_.mws.cnt_all, 0, sizeof(unsigned int), stream_);
   cudaMemsetAsync(ws_.hist, 0, sizeof(unsigned int) * (PINS_HIST_NB + 1), stream_);
+  cudaMemsetAsync(ws_.sw.colcnt, 0, sizeof(int) * n, stream_);
   int len = SC_ROWRES + t1cap + 8;
   if (len > h_scal_len_) {
     if (h_scal_) cudaFreeHost(h_scal_);
@@ -603,7 +604,8 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         const double gtd = h_scal_[SC_DOTS + 0];
         const double adot = h_scal_[SC_DOTS + 1];
         const double dsum = h_scal_[SC_TRIAL + 3];
-        const double dP = alpha * adot - eta_ * dsum;
+        // the trial pass's d term: sum X~ expm1(t) (FP64) or sum X~ (expm1(t) - t) (mixed)
+        const double dP = mixed_ ? alpha * gtd - eta_ * dsum : alpha * adot - eta_ * dsum;
         if (std::isfinite(dP) && dP >= cfg.armijo_c1 * alpha * gtd) { accepted = true; break; }
         alpha *= cfg.armijo_beta;
       }
@@ -775,12 +777,22 @@ pins_status Solver::step_objective_increase(const pins_config& cfg, const pins_p
   cudaMemcpyAsync(ws_.ab, a_, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
   cudaMemcpyAsync(ws_.ab + m_, b_, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
   prep(s);
+  if (mixed_) {
+    // the mixed trial pass returns sum X~ (expm1(t) - t); the linear part is
+    // alpha <grad, d> with grad = (a - r, b - c) at the current point
+    marg(s, false);
+    launch_grad(a_, b_, ws_.r, ws_.c, m_, n_, ws_.grad, stream_);
+    launch_dot2(ws_.grad, ws_.dir, nullptr, nullptr, m_ + n_, ws_.scal + SC_DOTS, stream_);
+    launches_ += 2;
+  } else {
+    launch_dot2(ws_.ab, ws_.dir, nullptr, nullptr, m_ + n_, ws_.scal + SC_DOTS, stream_);
+    ++launches_;
+  }
   launch_trial_prep(ws_.dir, m_, n_, alpha / eta_, mixed_ ? nullptr : ws_.Pt64,
                     mixed_ ? nullptr : ws_.Qt64, mixed_ ? ws_.Ptdd : nullptr,
                     mixed_ ? ws_.Qtdd : nullptr, stream_);
   marg(s, true);
-  launch_dot2(ws_.ab, ws_.dir, nullptr, nullptr, m_ + n_, ws_.scal + SC_DOTS, stream_);
-  launches_ += 2;
+  ++launches_;
   cudaMemcpyAsync(h_scal_, ws_.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if ((st = sync("step_objective_increase")) != PINS_OK) return st;
   double dP = alpha * h_scal_[SC_DOTS] - eta_ * h_scal_[SC_TRIAL + 3];

@@ -6,6 +6,7 @@
 // FP64 on GB300 runs at ~1/64 of the FP32 rate (~19 SM-cycles per warp-wide FP64
 // instruction), so scalar bookkeeping is done by one thread and broadcast, and the
 // vector work is spread over a thread-block cluster.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include "pins_kernels.h"
 
@@ -13,146 +14,112 @@ namespace cg = cooperative_groups;
 
 namespace pins {
 
-// exclusive scan of cnt[0..len) into ptr[0..len], resets cnt to 0
+// exclusive scan of cnt[0..len) into ptr[0..len], resets cnt to 0.  One CTA:
+// each thread owns a contiguous chunk, chunk totals are scanned with warp
+// shuffles, then every chunk is written from its offset.
 __global__ void __launch_bounds__(1024) k_scan(int* cnt, int* ptr, int len) {
-  __shared__ int sh[1024];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < len; base += 1024) {
-    int t = base + threadIdx.x;
-    int v = (t < len) ? cnt[t] : 0;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      int add = (threadIdx.x >= o) ? sh[threadIdx.x - o] : 0;
-      __syncthreads();
-      sh[threadIdx.x] += add;
-      __syncthreads();
-    }
-    if (t < len) { ptr[t] = carry + sh[threadIdx.x] - v; cnt[t] = 0; }
-    __syncthreads();
-    if (threadIdx.x == 0) carry += sh[1023];
-    __syncthreads();
+  __shared__ int wsum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (len + 1023) / 1024;
+  const int b0 = min(len, tid * per), b1 = min(len, b0 + per);
+  int tot = 0;
+  for (int t = b0; t < b1; ++t) tot += cnt[t];
+  int inc = tot;                                   // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
   }
-  if (threadIdx.x == 0) ptr[len] = carry;
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    wsum[lane] = w;                                // inclusive warp totals
+  }
+  __syncthreads();
+  int run = inc - tot + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int t = b0; t < b1; ++t) { const int v = cnt[t]; ptr[t] = run; run += v; cnt[t] = 0; }
+  if (tid == 1023) ptr[len] = wsum[31];
 }
 void launch_scan(int* cnt, int* ptr, int len, cudaStream_t st) {
   k_scan<<<1, 1024, 0, st>>>(cnt, ptr, len);
 }
 
 // ------------------------------------------------------------------------- //
-// CSC from the row-ordered CSR.  Up to PINS_CSC_SMEM entries: one CTA sorts the
-// keys (j << 32 | i) by a bitonic network in shared memory (payload: CSR
-// position) and derives colptr from the sorted columns.  Larger: a stable
-// counting sort over row chunks.  Either way the rows of a column come out
-// ascending, independent of timing.
+// CSC from the row-ordered CSR, in four launches: column counts (atomics),
+// exclusive scan (colptr; the counts are reset), placement (an atomic slot per
+// entry, so the order inside a column depends on timing), then every column's
+// entries sorted by row (a warp per column).  Rows are unique within a column,
+// so the result is the same on every run.  colcnt is zero on entry and on exit.
 // ------------------------------------------------------------------------- //
-#define PINS_CSC_SMEM 16384
-
-__global__ void __launch_bounds__(1024)
-k_csc_sort(const int* indptr, const int* indices, const double* data, int m, int n,
-           int* colptr, int* rowidx, double* cdata) {
-  extern __shared__ unsigned char csc_smem[];
+__global__ void k_csc_count(const int* indptr, const int* indices, int m, int* colcnt) {
   const int K = indptr[m];
-  unsigned int P2 = 1;
-  while (P2 < (unsigned int)K) P2 <<= 1;
-  unsigned long long* key = reinterpret_cast<unsigned long long*>(csc_smem);
-  int* pos = reinterpret_cast<int*>(key + P2);
-  for (int i = threadIdx.x; i < m; i += blockDim.x)
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K; e += gridDim.x * blockDim.x)
+    atomicAdd(colcnt + indices[e], 1);
+}
+__global__ void k_csc_place(const int* indptr, const int* indices, const double* data, int m,
+                            const int* colptr, int* fill, int* trow, double* tval) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
     for (int e = indptr[i]; e < indptr[i + 1]; ++e) {
-      key[e] = ((unsigned long long)(unsigned int)indices[e] << 32) | (unsigned int)i;
-      pos[e] = e;
+      const int j = indices[e];
+      const int pos = colptr[j] + atomicAdd(fill + j, 1);
+      trow[pos] = i;
+      tval[pos] = data[e];
     }
-  for (unsigned int q = K + threadIdx.x; q < P2; q += blockDim.x) { key[q] = ~0ull; pos[q] = -1; }
-  __syncthreads();
-  for (unsigned int k = 2; k <= P2; k <<= 1) {
-    for (unsigned int jv = k >> 1; jv > 0; jv >>= 1) {
-      for (unsigned int t = threadIdx.x; t < P2; t += blockDim.x) {
-        unsigned int l = t ^ jv;
-        if (l > t) {
-          bool up = ((t & k) == 0);
-          unsigned long long ka = key[t], kb = key[l];
-          if (up ? (ka > kb) : (ka < kb)) {
-            key[t] = kb; key[l] = ka;
-            int pa = pos[t]; pos[t] = pos[l]; pos[l] = pa;
+}
+__global__ void k_csc_segsort(const int* colptr, int n, int* fill, const int* trow,
+                              const double* tval, int* rowidx, double* cdata) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw) {
+    const int b = colptr[j], len = colptr[j + 1] - b;
+    if (lane == 0) fill[j] = 0;
+    if (len <= 32) {
+      int r = (lane < len) ? trow[b + lane] : 0x7fffffff;
+      double v = (lane < len) ? tval[b + lane] : 0.0;
+      if (len > 1) {
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+          for (int h = k >> 1; h > 0; h >>= 1) {
+            const int rk = __shfl_xor_sync(0xffffffffu, r, h);
+            const double vk = __shfl_xor_sync(0xffffffffu, v, h);
+            const bool up = (lane & k) == 0, low = (lane & h) == 0;
+            const bool take = low ? (up ? rk < r : rk > r) : (up ? rk > r : rk < r);
+            if (take) { r = rk; v = vk; }
           }
         }
       }
-      __syncthreads();
-    }
-  }
-  for (int q = threadIdx.x; q < K; q += blockDim.x) {
-    const int j = (int)(key[q] >> 32);
-    rowidx[q] = (int)(key[q] & 0xffffffffu);
-    cdata[q] = data[pos[q]];
-    const int jprev = (q == 0) ? -1 : (int)(key[q - 1] >> 32);
-    for (int c = jprev + 1; c <= j; ++c) colptr[c] = q;      // columns starting here
-    if (q == K - 1) for (int c = j + 1; c <= n; ++c) colptr[c] = K;
-  }
-  if (K == 0) for (int c = threadIdx.x; c <= n; c += blockDim.x) colptr[c] = 0;
-}
-
-__device__ __forceinline__ void chunk_rows(int c, int chunks, int m, int& r0, int& r1) {
-  const int R = (m + chunks - 1) / chunks;
-  r0 = min(m, c * R);
-  r1 = min(m, r0 + R);
-}
-__global__ void k_csc_count(const int* indptr, const int* indices, int m, int n, int chunks,
-                            int* cnt) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += gridDim.x * blockDim.x) {
-    int r0, r1; chunk_rows(c, chunks, m, r0, r1);
-    for (int e = indptr[r0]; e < indptr[r1]; ++e) cnt[(size_t)c * n + indices[e]] += 1;
-  }
-}
-__global__ void k_csc_colscan(int* cnt, int chunks, int n, int* coltot) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    int run = 0;
-    for (int c = 0; c < chunks; ++c) {
-      int v = cnt[(size_t)c * n + j];
-      cnt[(size_t)c * n + j] = run;
-      run += v;
-    }
-    coltot[j] = run;
-  }
-}
-__global__ void k_csc_scatter(const int* indptr, const int* indices, const double* data, int m,
-                              int n, int chunks, int* off, const int* colptr, int* rowidx,
-                              double* cdata) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += gridDim.x * blockDim.x) {
-    int r0, r1; chunk_rows(c, chunks, m, r0, r1);
-    for (int i = r0; i < r1; ++i)
-      for (int e = indptr[i]; e < indptr[i + 1]; ++e) {
-        const int j = indices[e];
-        const int pos = colptr[j] + off[(size_t)c * n + j]++;
-        rowidx[pos] = i;
-        cdata[pos] = data[e];
+      if (lane < len) { rowidx[b + lane] = r; cdata[b + lane] = v; }
+    } else {
+      // long column: each entry's rank is the number of smaller rows
+      for (int q = lane; q < len; q += 32) {
+        const int r = trow[b + q];
+        int rank = 0;
+        for (int t = 0; t < len; ++t) rank += (trow[b + t] < r) ? 1 : 0;
+        rowidx[b + rank] = r;
+        cdata[b + rank] = tval[b + q];
       }
+    }
   }
 }
 
 void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
                         int nnz, const SparseWS& sw, cudaStream_t st) {
-  if (nnz <= PINS_CSC_SMEM) {
-    unsigned int P2 = 1;
-    while (P2 < (unsigned int)nnz) P2 <<= 1;
-    const size_t smem = (size_t)P2 * (sizeof(unsigned long long) + sizeof(int));
-    static bool configured = false;
-    if (!configured) {
-      cudaFuncSetAttribute(k_csc_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((size_t)PINS_CSC_SMEM * 12));
-      configured = true;
-    }
-    k_csc_sort<<<1, 1024, smem, st>>>(indptr, indices, data, m, n, sw.colptr, sw.rowidx, sw.cdata);
-    return;
-  }
-  const int chunks = m < PINS_CSC_CHUNKS ? m : PINS_CSC_CHUNKS;
-  cudaMemsetAsync(sw.chunkcnt, 0, sizeof(int) * (size_t)chunks * n, st);
-  k_csc_count<<<(chunks + 255) / 256, 256, 0, st>>>(indptr, indices, m, n, chunks, sw.chunkcnt);
-  k_csc_colscan<<<(n + 255) / 256, 256, 0, st>>>(sw.chunkcnt, chunks, n, sw.colcnt);
+  const int cb = std::max(1, std::min((nnz + 255) / 256, 1184));
+  k_csc_count<<<cb, 256, 0, st>>>(indptr, indices, m, sw.colcnt);
   k_scan<<<1, 1024, 0, st>>>(sw.colcnt, sw.colptr, n);
-  k_csc_scatter<<<(chunks + 255) / 256, 256, 0, st>>>(indptr, indices, data, m, n, chunks,
-                                                      sw.chunkcnt, sw.colptr, sw.rowidx, sw.cdata);
+  const int pb = std::max(1, std::min((m + 255) / 256, 1184));
+  k_csc_place<<<pb, 256, 0, st>>>(indptr, indices, data, m, sw.colptr, sw.colcnt, sw.trow,
+                                  sw.tval);
+  const int sb = std::max(1, std::min((n + 7) / 8, 2368));
+  k_csc_segsort<<<sb, 256, 0, st>>>(sw.colptr, n, sw.colcnt, sw.trow, sw.tval, sw.rowidx,
+                                    sw.cdata);
 }
 
 // ------------------------------------------------------------------------- //
