@@ -35,7 +35,7 @@ namespace pins {
 #define PINS_DDCG_MAX 16
 #define PINS_DDCG_TPB 256
 #define PINS_DDCG_SMEM (200 * 1024)
-// shared bytes per unknown: u (4) + r, x, p, s, w, diag, od (7 x 8) + D^-1 (4) + row begin (4)
+// shared bytes per unknown: r, x, p, s, w, diag, od (7 x 8) + u (4) + D^-1 (4) + row begin (4)
 #define PINS_DDCG_PER_UNKNOWN 68
 
 struct CGddArgs {
@@ -46,6 +46,9 @@ struct CGddArgs {
   const int* colptr; const int* rowidx; const double* cdata;
   const double* rhs; double* x;
   int* ent_tgt; float2* ent_val;   // scratch: one slot per entry of the CSR + CSC entry space
+  int* ent_row;
+  float* ug;                       // u of every unknown (N floats), the exchange buffer
+  size_t smem_bytes;               // dynamic shared memory of the launch
   float rtol2; int max_iter; double* info;
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
 };
@@ -105,7 +108,6 @@ __device__ __forceinline__ float2 ddv_add(float2 a, float2 b) {
 __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
-  __shared__ float* rem_u[PINS_DDCG_MAX];
   __shared__ float slot[3 * PINS_DDCG_MAX];
   __shared__ unsigned int eslot[1];
   __shared__ float red[3][PINS_DDCG_TPB / 32];
@@ -119,17 +121,21 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   const int L = (N + CS - 1) / CS;
   const int lo = rank * L;
   const int nl = max(0, min(N, lo + L) - lo);
+  // shared memory: the own slice (7 double-float and 2 FP32 arrays of L4, L4 + 4
+  // row offsets), then, when the dynamic allocation has room, this CTA's packed
+  // entries (target, value / eta, local row)
+  const int L4 = (L + 3) & ~3;
   float2* rv = reinterpret_cast<float2*>(ddcg_smem);
-  float2* xv = rv + L;
-  float2* pv = xv + L;
-  float2* sv = pv + L;
-  float2* wv = sv + L;
-  float2* dg = wv + L;        // diag / eta
-  float2* od = dg + L;        // off-diagonal part of M u (zeroed after use)
-  float* u = reinterpret_cast<float*>(od + L);   // read by other CTAs
-  float* dinv = u + L;
-  int* rb = reinterpret_cast<int*>(dinv + L);    // L + 1 entry offsets (relative to E0)
-  if (tid < CS) rem_u[tid] = cluster.map_shared_rank(u, tid);
+  float2* xv = rv + L4;
+  float2* pv = xv + L4;
+  float2* sv = pv + L4;
+  float2* wv = sv + L4;
+  float2* dg = wv + L4;       // diag / eta
+  float2* od = dg + L4;       // off-diagonal part of M u (zeroed after use)
+  float* u = reinterpret_cast<float*>(od + L4);  // own slice (also published in a.ug)
+  float* dinv = u + L4;
+  int* rb = reinterpret_cast<int*>(dinv + L4);   // nl + 1 entry offsets (relative to E0)
+  const size_t base_bytes = sizeof(float) * (size_t)(PINS_DDCG_PER_UNKNOWN / 4) * L4 + 16;
 
   const int Kc = __ldg(a.indptr + m);
   auto beg = [&](int t) -> int {
@@ -154,6 +160,16 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // ---- own unknowns: diagonal, preconditioner, residual, row offsets ----
   const int E0 = beg(min(lo, N));
   const int E1 = beg(min(lo + nl, N));
+  // ---- entries of the own unknowns: packed (owner, offset) and value / eta, in
+  // shared memory when they fit, else in the global scratch ----
+  const size_t used = base_bytes;
+  const bool ent_local = used + (2 * sizeof(int) + sizeof(float2)) * (size_t)(E1 - E0) <= a.smem_bytes;
+  float2* ev_s = reinterpret_cast<float2*>(ddcg_smem + used);
+  int* et_s = reinterpret_cast<int*>(ev_s + (E1 - E0));
+  int* er_s = et_s + (E1 - E0);
+  int* etg = ent_local ? et_s : a.ent_tgt + E0;
+  float2* eva = ent_local ? ev_s : a.ent_val + E0;
+  int* erow = ent_local ? er_s : a.ent_row + E0;   // local unknown of each entry
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
     const int t = lo + k;
     const double d = (t < m) ? __ldg(a.r + t) : __ldg(a.c + t - m);
@@ -164,22 +180,22 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     pv[k] = make_float2(0.f, 0.f);
     sv[k] = make_float2(0.f, 0.f);
     od[k] = make_float2(0.f, 0.f);
-    rb[k] = beg(t) - E0;
+    const int b0 = beg(t) - E0, b1 = beg(t + 1) - E0;
+    rb[k] = b0;
+    for (int e = b0; e < b1; ++e) erow[e] = k;
   }
   if (tid == 0) rb[nl] = E1 - E0;
-  // ---- entries of the own unknowns: packed (owner, offset) and value / eta ----
   for (int e = E0 + tid; e < E1; e += PINS_DDCG_TPB) {
     int g; double v;
     if (e < Kc) { v = __ldg(a.data + e); g = m + __ldg(a.indices + e); }
     else { v = __ldg(a.cdata + e - Kc); g = __ldg(a.rowidx + e - Kc); }
-    int ow = g / L, off = g - ow * L;
     float2 val = ddv_mul(split_f64(v, 0), ie);
-    if (g < 0 || g >= N || ow >= CS || off >= L) {
+    if (g < 0 || g >= N) {
       atomicOr(a.flag, 1);
-      ow = rank; off = 0; val = make_float2(0.f, 0.f);
+      g = 0; val = make_float2(0.f, 0.f);
     }
-    a.ent_tgt[e] = (ow << 16) | off;
-    a.ent_val[e] = val;
+    etg[e - E0] = g;
+    eva[e - E0] = val;
   }
   // first cluster barrier: every CTA has started (no distributed shared memory
   // access precedes it) and has published its block maximum
@@ -192,6 +208,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     const float2 r0 = split_f64(a.rhs[lo + k], shift);
     rv[k] = r0;
     u[k] = __fmul_rn(dinv[k], r0.x);
+    __stcg(a.ug + lo + k, u[k]);
   }
   // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
   const int ne = E1 - E0;
@@ -208,44 +225,53 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     t0 = lo_s;
   }
   const bool starts_mid = (c0 < c1) && rb[t0] < c0;
-  // written above by this CTA: plain (coherent) loads, not the read-only path
-  const int* etg = a.ent_tgt + E0;
-  const float2* eva = a.ent_val + E0;
 
-  // od[t] = sum over the row/column entries of (S/eta) u, for the own unknowns
+  // od[t] = sum over the row/column entries of (S/eta) u, for the own unknowns.
+  // Products first (independent), then a sum over runs of equal local row; a
+  // row cut by the slice start is this thread's head, a row cut by its end its
+  // tail (completed below from the following threads' heads, in thread order).
   auto spmv = [&]() {
-    int t = t0;
-    bool first = true;
-    float2 acc = make_float2(0.f, 0.f);
     float2 headv = make_float2(0.f, 0.f), tailv = make_float2(0.f, 0.f);
     int headrow = -1, tailrow = -1;
-    auto close_row = [&](bool ended_inside) {
-      if (first && starts_mid) { headrow = t; headv = acc; }
-      else if (!ended_inside) { tailrow = t; tailv = acc; }
-      else od[t] = acc;
-      first = false;
-      acc = make_float2(0.f, 0.f);
-    };
-    for (int base = c0; base < c1; base += 4) {
-      int tg[4]; float2 v[4]; float uu[4];
+    if (c0 < c1) {
+      int cur = erow[c0];
+      bool first = true;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int base = c0; base < c1; base += 4) {
+        int tg[4], rw[4]; float2 v[4]; float uu[4], ph[4], pl[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = base + q;
-        tg[q] = (e < c1) ? etg[e] : (rank << 16);
-        v[q] = (e < c1) ? eva[e] : make_float2(0.f, 0.f);
-      }
+        for (int q = 0; q < 4; ++q) {
+          const bool ok = base + q < c1;
+          tg[q] = ok ? etg[base + q] : 0;
+          v[q] = ok ? eva[base + q] : make_float2(0.f, 0.f);
+          rw[q] = ok ? erow[base + q] : cur;
+        }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) uu[q] = rem_u[tg[q] >> 16][tg[q] & 0xffff];
+        for (int q = 0; q < 4; ++q) uu[q] = __ldcg(a.ug + tg[q]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = base + q;
-        if (e < c1) {
-          while (rb[t + 1] <= e) { close_row(true); ++t; }
-          ddv_acc_mul(acc, v[q], uu[q]);
+        for (int q = 0; q < 4; ++q) {
+          two_prod(v[q].x, uu[q], ph[q], pl[q]);
+          pl[q] = __fmaf_rn(v[q].y, uu[q], pl[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (base + q < c1) {
+            if (rw[q] != cur) {                     // row cur ended inside the slice
+              if (first && starts_mid) { headrow = cur; headv = acc; }
+              else od[cur] = acc;
+              first = false;
+              acc = make_float2(0.f, 0.f);
+              cur = rw[q];
+            }
+            float t1, t2; two_sum(acc.x, ph[q], t1, t2);
+            acc.x = t1; acc.y = __fadd_rn(acc.y, __fadd_rn(t2, pl[q]));
+          }
         }
       }
+      if (first && starts_mid) { headrow = cur; headv = acc; }
+      else if (rb[cur + 1] > c1) { tailrow = cur; tailv = acc; }
+      else od[cur] = acc;
     }
-    if (c0 < c1) close_row(rb[t + 1] <= c1);
     hrow[tid] = (c0 < c1) ? headrow : -2;           // -2: empty slice, skipped below
     hval[tid] = headv;
     __syncthreads();
@@ -304,18 +330,30 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // w = diag u + od, od reset; partial inner products
   auto apply_w = [&](float& lg, float& ld, float& lrr) {
     lg = 0.f; ld = 0.f; lrr = 0.f;
-    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-      const float uk = u[k];
-      float2 w = od[k];
-      ddv_acc_mul(w, dg[k], uk);
-      float h, l; fast_two_sum(w.x, w.y, h, l);
-      w = make_float2(h, l);
-      wv[k] = w;
-      od[k] = make_float2(0.f, 0.f);
-      const float rk = rv[k].x;
-      lg = __fmaf_rn(rk, uk, lg);
-      ld = __fmaf_rn(w.x, uk, ld);
-      lrr = __fmaf_rn(rk, rk, lrr);
+    for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
+      const int k2 = k + PINS_DDCG_TPB;
+      const bool two = k2 < nl;
+      const int kk[2] = {k, two ? k2 : k};
+      float uk[2], rk[2]; float2 w[2], dgk[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uk[h] = u[kk[h]]; w[h] = od[kk[h]]; dgk[h] = dg[kk[h]]; rk[h] = rv[kk[h]].x;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        ddv_acc_mul(w[h], dgk[h], uk[h]);
+        float hh, ll; fast_two_sum(w[h].x, w[h].y, hh, ll);
+        w[h] = make_float2(hh, ll);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        wv[kk[h]] = w[h];
+        od[kk[h]] = make_float2(0.f, 0.f);
+        lg = __fmaf_rn(rk[h], uk[h], lg);
+        ld = __fmaf_rn(w[h].x, uk[h], ld);
+        lrr = __fmaf_rn(rk[h], rk[h], lrr);
+      }
     }
   };
 
@@ -331,15 +369,32 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   int it = 0;
   bool stop = !(bb > 0.f);
   while (!stop && it < a.max_iter) {
-    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-      const float uk = u[k];
-      float2 p = ddv_axpy(beta, pv[k], make_float2(uk, 0.f));
-      float2 s = ddv_axpy(beta, sv[k], wv[k]);
-      pv[k] = p; sv[k] = s;
-      xv[k] = ddv_axpy(alpha, p, xv[k]);
-      const float2 r1 = ddv_axpy(-alpha, s, rv[k]);
-      rv[k] = r1;
-      u[k] = __fmul_rn(dinv[k], r1.x);
+    // two unknowns per step, loads first, so their dependency chains overlap
+    for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
+      const int k2 = k + PINS_DDCG_TPB;
+      const bool two = k2 < nl;
+      const int kk[2] = {k, two ? k2 : k};
+      float uk[2], di[2]; float2 p0[2], s0[2], w0[2], x0[2], r0[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uk[h] = u[kk[h]]; di[h] = dinv[kk[h]]; p0[h] = pv[kk[h]]; s0[h] = sv[kk[h]];
+        w0[h] = wv[kk[h]]; x0[h] = xv[kk[h]]; r0[h] = rv[kk[h]];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        p0[h] = ddv_axpy(beta, p0[h], make_float2(uk[h], 0.f));
+        s0[h] = ddv_axpy(beta, s0[h], w0[h]);
+        x0[h] = ddv_axpy(alpha, p0[h], x0[h]);
+        r0[h] = ddv_axpy(-alpha, s0[h], r0[h]);
+        uk[h] = __fmul_rn(di[h], r0[h].x);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !two) break;
+        pv[kk[h]] = p0[h]; sv[kk[h]] = s0[h]; xv[kk[h]] = x0[h]; rv[kk[h]] = r0[h];
+        u[kk[h]] = uk[h];
+        __stcg(a.ug + lo + kk[h], uk[h]);
+      }
     }
     ++it;
     cluster.sync();                                 // every u slice updated
@@ -387,27 +442,29 @@ static int ddcg_cluster_size() {
 }
 
 size_t ddcg_smem_bytes(int N, int cs) {
-  const int L = (N + cs - 1) / cs;
-  return (size_t)PINS_DDCG_PER_UNKNOWN * L + 16;
+  const int L4 = (((N + cs - 1) / cs) + 3) & ~3;
+  return (size_t)PINS_DDCG_PER_UNKNOWN * L4 + 16;
 }
 
 cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
                           const double* rhs, double* x, int* ent_tgt, float2* ent_val,
-                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
-                          bool* used) {
+                          int* ent_row, float* ug, double rtol, int max_iter, double* info,
+                          int* flag, cudaStream_t st, bool* used) {
   *used = false;
   const int N = m + n;
   const int CS = ddcg_cluster_size();
   const int L = (N + CS - 1) / CS;
-  const size_t smem = ddcg_smem_bytes(N, CS);
-  if (smem > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
+  if (ddcg_smem_bytes(N, CS) > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
+  const size_t smem = PINS_DDCG_SMEM;   // the rest holds a copy of u and the entries when they fit
   CGddArgs a;
   a.m = m; a.n = n; a.inv_eta = 1.0 / eta;
   a.r = r; a.c = c; a.indptr = indptr; a.indices = indices; a.data = data;
   a.colptr = colptr; a.rowidx = rowidx; a.cdata = cdata;
-  a.rhs = rhs; a.x = x; a.ent_tgt = ent_tgt; a.ent_val = ent_val;
+  a.rhs = rhs; a.x = x; a.ent_tgt = ent_tgt; a.ent_val = ent_val; a.ent_row = ent_row;
+  a.ug = ug;
+  a.smem_bytes = smem;
   a.rtol2 = (float)(rtol * rtol); a.max_iter = max_iter; a.info = info; a.flag = flag;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(CS);

@@ -303,6 +303,8 @@ struct PassArgs {
   const double* F; const double* G;       // potentials
   const double* A64; const double* B64;   // FP64: A = F/eta - s, B = G/eta
   const float2* Add; const float2* Bdd;   // mixed: same as double-float pairs
+  const float2* A2dd; const float2* B2dd; // mixed Sinkhorn: log2(e) A, log2(e) B
+  dd kappa2_dd;                           // log2(e) kappa_dd
   const double* a; const double* b;
   const float2* exp_table;                // 2^(q/1024) pairs (mixed)
 };

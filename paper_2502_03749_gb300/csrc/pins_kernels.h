@@ -46,8 +46,8 @@ cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* 
                        const int* indptr, const int* indices, const double* data,
                        const int* colptr, const int* rowidx, const double* cdata,
                        const double* rhs, double* x, double* res, double* p, double* q,
-                       double* part, double rtol, int max_iter, double* info, int sms,
-                       cudaStream_t st);
+                       double* part, double rtol, int max_iter, double* info, int* flag,
+                       int sms, cudaStream_t st);
 int cg_blocks(int N, int sms);
 // single-reduction cluster PCG (pins_cg.cu); *used = false when the system does
 // not fit one cluster's shared memory
@@ -62,8 +62,10 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
                           const double* rhs, double* x, int* ent_tgt, float2* ent_val,
-                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
-                          bool* used);
+                          int* ent_row, float* ug, double rtol, int max_iter, double* info,
+                          int* flag, cudaStream_t st, bool* used);
+void launch_prep2(const double* F, const double* G, int m, int n, double eta, double s,
+                  float2* A2dd, float2* B2dd, cudaStream_t st);
 void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
 void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,

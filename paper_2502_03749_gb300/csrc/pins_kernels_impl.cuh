@@ -59,6 +59,30 @@ template <int K> struct Launch {
   }
   static void marg(const PassArgs& p, const TileGeom& g, const MergeWS& ws, const TrialArgs* tr,
                    double* r, double* c, double* out4, cudaStream_t st) {
+    if constexpr (P::MIXED) {
+      // column segments of PINS_MSEG (at most g.gx: rowpart holds g.gx * m), row
+      // groups for one wave at 2 CTAs per SM (at most g.gy: colpart holds g.gy * n)
+      const int sx = (p.n + PINS_MSEG - 1) / PINS_MSEG;
+      if (sx <= g.gx) {
+        static bool configured = false;
+        if (!configured) {
+          cudaFuncSetAttribute(k_marg_mx<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PINS_MSEG_SMEM);
+          cudaFuncSetAttribute(k_marg_mx<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PINS_MSEG_SMEM);
+          configured = true;
+        }
+        const int gy = std::max(1, std::min({(2 * sm_count() + sx - 1) / sx, g.gy,
+                                             (p.m + PINS_WARPS - 1) / PINS_WARPS}));
+        if (tr) {
+          k_marg_mx<P, true><<<dim3(sx, gy), PINS_TPB, PINS_MSEG_SMEM, st>>>(p, ws, *tr, r, c, out4);
+        } else {
+          TrialArgs none{};
+          k_marg_mx<P, false><<<dim3(sx, gy), PINS_TPB, PINS_MSEG_SMEM, st>>>(p, ws, none, r, c, out4);
+        }
+        return;
+      }
+    }
     if (tr) k_marg<P, true><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, *tr, r, c, out4);
     else {
       TrialArgs none{};

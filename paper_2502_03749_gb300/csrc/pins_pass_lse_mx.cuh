@@ -1,12 +1,13 @@
 // Sinkhorn warm-up half-steps of the mixed policy (Algorithm 2 warm-up loop;
-// Algorithm 1 in log form), streamed with an online log-sum-exp.
+// Algorithm 1 in log form), streamed with an online log-sum-exp in base 2.
 //
-// Each thread keeps a running (M, S) with S = sum exp(w - M): an entry w below
-// M adds exp(w - M); an entry above M first rescales S by exp(M - w) (rare once
-// the running maximum has settled).  No tile of w is held in registers and no
-// per-tile maximum pass is needed, so the kernels stream C at one FP32 ex2 per
-// entry.  w = V - kappa C_ij is formed in double-float and the exponent
-// (w_hi - M) + w_lo in FP32, as in the tiled kernels.
+// The passes read log2(e) A_i, log2(e) B_j and log2(e) kappa as double-float
+// pairs, so w = V - kappa C_ij is formed in double-float directly in log2 units
+// and each entry costs one FP32 ex2 (flush-to-zero: a term below 2^-126 of the
+// running maximum is dropped).  Each thread keeps a running (M, S) with
+// S = sum 2^(w - M) and updates it four entries at a time: M' = max(M, the
+// four w), S = S 2^(M - M') + sum 2^((w_hi - M') + w_lo).  No branch, no tile
+// of w held in registers, no per-tile maximum pass.
 //
 // Row half-step: CTA (x, y) stages the B_j of column segment x in shared memory;
 // warp w takes rows y*8 + w + t*8*gridDim.y over that segment; a warp's (M, S)
@@ -21,16 +22,35 @@
 
 namespace pins {
 
-#define PINS_LSE_LOG2E 1.4426950408889634f
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
-__device__ __forceinline__ void lse_online(float& M, float& S, float wh, float wl) {
-  float d = __fsub_rn(wh, M);
-  if (d > 0.f) {                 // new running maximum (also the first entry: M = -inf)
-    S = __fmul_rn(S, exp2f(-d * PINS_LSE_LOG2E));
-    M = wh;
-    d = 0.f;
-  }
-  S = __fadd_rn(S, exp2f(__fadd_rn(d, wl) * PINS_LSE_LOG2E));
+// four entries into a running base-2 (M, S); every wh finite
+__device__ __forceinline__ void lse2_chunk(float& M, float& S, const float wh[4],
+                                           const float wl[4]) {
+  const float Mn = fmaxf(M, fmaxf(fmaxf(wh[0], wh[1]), fmaxf(wh[2], wh[3])));
+  float t = __fmul_rn(S, ex2_ftz(__fsub_rn(M, Mn)));    // M = -inf: 2^-inf = 0
+#pragma unroll
+  for (int q = 0; q < 4; ++q) t = __fadd_rn(t, ex2_ftz(__fadd_rn(__fsub_rn(wh[q], Mn), wl[q])));
+  S = t;
+  M = Mn;
+}
+// one entry (tails)
+__device__ __forceinline__ void lse2_one(float& M, float& S, float wh, float wl) {
+  const float Mn = fmaxf(M, wh);
+  S = __fadd_rn(__fmul_rn(S, ex2_ftz(__fsub_rn(M, Mn))), ex2_ftz(__fadd_rn(__fsub_rn(wh, Mn), wl)));
+  M = Mn;
+}
+// base-2 LSE pair merge
+__device__ __forceinline__ void lse2_merge(float& m1, float& s1, float m2, float s2) {
+  if (m2 == -INFINITY) return;
+  if (m1 == -INFINITY) { m1 = m2; s1 = s2; return; }
+  const float mn = fmaxf(m1, m2);
+  s1 = __fadd_rn(__fmul_rn(s1, ex2_ftz(__fsub_rn(m1, mn))), __fmul_rn(s2, ex2_ftz(__fsub_rn(m2, mn))));
+  m1 = mn;
 }
 
 // 4 consecutive raw costs of row i from column j (entries at or beyond jend are
@@ -61,20 +81,38 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
   const int m = p.m, n = p.n;
   const int x = blockIdx.x, y = blockIdx.y, SX = gridDim.x, GY = gridDim.y;
   const int j0 = x * seg, j1 = min(n, j0 + seg);
-  const float kh = p.kappa_dd.hi, kl = p.kappa_dd.lo;
-  for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = p.Bdd[j];
+  const float kh = p.kappa2_dd.hi, kl = p.kappa2_dd.lo;
+  for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = p.B2dd[j];
   __syncthreads();
   for (int i = y * PINS_WARPS + warp; i < m; i += GY * PINS_WARPS) {
     float M = -INFINITY, S = 0.f;
-    for (int jb = j0 + 4 * lane; jb < j1; jb += 128) {
+    int jb = j0 + 4 * lane;
+    // two chunks of 4 per step: both loads issued before either update
+    for (; jb + 128 + 3 < j1; jb += 256) {
+      float c0[4], c1[4];
+      cost4<P>(p, i, jb, j1, c0);
+      cost4<P>(p, i, jb + 128, j1, c1);
+      float wh[4], wl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dd_w(sB[jb + q - j0], c0[q], kh, kl, wh[q], wl[q]);
+      lse2_chunk(M, S, wh, wl);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dd_w(sB[jb + 128 + q - j0], c1[q], kh, kl, wh[q], wl[q]);
+      lse2_chunk(M, S, wh, wl);
+    }
+    for (; jb < j1; jb += 128) {
       float c[4];
       cost4<P>(p, i, jb, j1, c);
+      if (jb + 3 < j1) {
+        float wh[4], wl[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (jb + q < j1) {
+        for (int q = 0; q < 4; ++q) dd_w(sB[jb + q - j0], c[q], kh, kl, wh[q], wl[q]);
+        lse2_chunk(M, S, wh, wl);
+      } else {
+        for (int q = 0; jb + q < j1; ++q) {
           float wh, wl;
           dd_w(sB[jb + q - j0], c[q], kh, kl, wh, wl);
-          lse_online(M, S, wh, wl);
+          lse2_one(M, S, wh, wl);
         }
       }
     }
@@ -82,12 +120,13 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
     for (int o = 16; o > 0; o >>= 1) {
       const float Mo = __shfl_xor_sync(0xffffffffu, M, o);
       const float So = __shfl_xor_sync(0xffffffffu, S, o);
-      lse_merge_f(M, S, Mo, So);
+      lse2_merge(M, S, Mo, So);
     }
     if (lane == 0) store_f2(ws.rowpart0 + (size_t)x * m + i, M, S);
   }
   // merge the segments of this row group (last of its SX CTAs)
   if (arrive_last(ws.cnt_row + y, SX)) {
+    const double LN2 = 0.69314718055994530942;
     double res = 0.0;
     const int per = PINS_WARPS * ((m + GY * PINS_WARPS - 1) / (GY * PINS_WARPS));
     for (int k = threadIdx.x; k < per; k += PINS_TPB) {
@@ -96,13 +135,13 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
       float Mf = -INFINITY, Sf = 0.f;
       for (int xs = 0; xs < SX; ++xs) {
         const float2 o = load_f2_cg(ws.rowpart0 + (size_t)xs * m + i);
-        lse_merge_f(Mf, Sf, o.x, o.y);
+        lse2_merge(Mf, Sf, o.x, o.y);
       }
-      const double lse = (double)Mf + log((double)Sf);
-      const double A = (double)p.Add[i].x + (double)p.Add[i].y;
+      const double lse2 = (double)Mf + log2((double)Sf);         // base-2 LSE_j of w
+      const double A2 = (double)p.A2dd[i].x + (double)p.A2dd[i].y;
       const double ai = p.a[i];
-      res += fabs(exp(A + lse) - ai);
-      F_out[i] = p.eta * (log(ai) + p.s - lse);
+      res += fabs(exp2(A2 + lse2) - ai);
+      F_out[i] = p.eta * (log(ai) + p.s - LN2 * lse2);
     }
     const double br = block_sum(res, sh_red);
     if (threadIdx.x == 0) ws.scal_row[y] = br;
@@ -123,43 +162,54 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
   const int m = p.m, n = p.n;
   const int i0 = blockIdx.y * rb, i1 = min(m, i0 + rb);
   const int nct = (n + PINS_TC - 1) / PINS_TC;
-  const float kh = p.kappa_dd.hi, kl = p.kappa_dd.lo;
+  const float kh = p.kappa2_dd.hi, kl = p.kappa2_dd.lo;
   for (int ct = blockIdx.x; ct < nct; ct += gridDim.x) {
     const int jb = ct * PINS_TC + 4 * lane;
+    const int nv = min(4, n - jb);                 // valid columns of this lane (may be <= 0)
     float M[4], S[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) { M[q] = -INFINITY; S[q] = 0.f; }
-    int i = i0 + warp;
-    // four rows per step: loads first, then the updates
-    for (; i + 3 * PINS_WARPS < i1; i += 4 * PINS_WARPS) {
-      float c[4][4];
-      float2 A[4];
+    if (nv >= 4) {
+      int i = i0 + warp;
+      // four rows per step: loads first, then a chunk update per column
+      for (; i + 3 * PINS_WARPS < i1; i += 4 * PINS_WARPS) {
+        float c[4][4];
+        float2 A[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        A[t] = p.Add[i + t * PINS_WARPS];
-        cost4<P>(p, i + t * PINS_WARPS, jb, n, c[t]);
+        for (int t = 0; t < 4; ++t) {
+          A[t] = p.A2dd[i + t * PINS_WARPS];
+          cost4<P>(p, i + t * PINS_WARPS, jb, n, c[t]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float wh[4], wl[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) dd_w(A[t], c[t][q], kh, kl, wh[t], wl[t]);
+          lse2_chunk(M[q], S[q], wh, wl);
+        }
       }
+      for (; i < i1; i += PINS_WARPS) {
+        float c[4];
+        const float2 A = p.A2dd[i];
+        cost4<P>(p, i, jb, n, c);
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (jb + q < n) {
-            float wh, wl;
-            dd_w(A[t], c[t][q], kh, kl, wh, wl);
-            lse_online(M[q], S[q], wh, wl);
-          }
-    }
-    for (; i < i1; i += PINS_WARPS) {
-      float c[4];
-      const float2 A = p.Add[i];
-      cost4<P>(p, i, jb, n, c);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (jb + q < n) {
+        for (int q = 0; q < 4; ++q) {
           float wh, wl;
           dd_w(A, c[q], kh, kl, wh, wl);
-          lse_online(M[q], S[q], wh, wl);
+          lse2_one(M[q], S[q], wh, wl);
         }
+      }
+    } else if (nv > 0) {
+      for (int i = i0 + warp; i < i1; i += PINS_WARPS) {
+        float c[4];
+        const float2 A = p.A2dd[i];
+        cost4<P>(p, i, jb, n, c);
+        for (int q = 0; q < nv; ++q) {
+          float wh, wl;
+          dd_w(A, c[q], kh, kl, wh, wl);
+          lse2_one(M[q], S[q], wh, wl);
+        }
+      }
     }
     // merge the 8 warps per column, in warp order
 #pragma unroll
@@ -168,7 +218,7 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
     if (threadIdx.x < PINS_TC) {
       float Mc = -INFINITY, Sc = 0.f;
 #pragma unroll
-      for (int w = 0; w < PINS_WARPS; ++w) lse_merge_f(Mc, Sc, stg[w][threadIdx.x].x, stg[w][threadIdx.x].y);
+      for (int w = 0; w < PINS_WARPS; ++w) lse2_merge(Mc, Sc, stg[w][threadIdx.x].x, stg[w][threadIdx.x].y);
       const int j = ct * PINS_TC + threadIdx.x;
       if (j < n) store_f2(ws.colpart0 + (size_t)blockIdx.y * n + j, Mc, Sc);
     }
@@ -176,15 +226,16 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
   }
   // merge the row blocks of this CTA's strips (last of the gridDim.y CTAs)
   if (arrive_last(ws.cnt_col + blockIdx.x, gridDim.y)) {
+    const double LN2 = 0.69314718055994530942;
     for (int ct = blockIdx.x; ct < nct; ct += gridDim.x) {
       const int j = ct * PINS_TC + threadIdx.x;
       if (threadIdx.x < PINS_TC && j < n) {
         float Mf = -INFINITY, Sf = 0.f;
         for (int yb = 0; yb < (int)gridDim.y; ++yb) {
           const float2 o = load_f2_cg(ws.colpart0 + (size_t)yb * n + j);
-          lse_merge_f(Mf, Sf, o.x, o.y);
+          lse2_merge(Mf, Sf, o.x, o.y);
         }
-        G_out[j] = p.eta * (log(p.b[j]) - ((double)Mf + log((double)Sf)));
+        G_out[j] = p.eta * (log(p.b[j]) - LN2 * ((double)Mf + log2((double)Sf)));
       }
     }
   }

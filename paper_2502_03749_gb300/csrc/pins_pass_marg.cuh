@@ -102,18 +102,25 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
             if constexpr (TRIAL) {
               float th, tl; two_sum(Pt.x, Qf[q].x, th, tl);
               tl = __fadd_rn(tl, __fadd_rn(Pt.y, Qf[q].y));
-              // objective term X~ (expm1(t) - t) >= 0: FP32 suffices (no cancellation)
-              const float ef = exp2f(__fadd_rn(zh, zl) * 1.4426950408889634f);
-              dfs = __fmaf_rn(ef, expm1_minus_x(__fadd_rn(th, tl)), dfs);
+              const float z0 = __fadd_rn(zh, zl);
+              const float tf = __fadd_rn(th, tl);
               // trial point z + t in double-float
               float sh, se; two_sum(zh, th, sh, se);
               se = __fadd_rn(se, __fadd_rn(zl, tl));
               fast_two_sum(sh, se, zh, zl);
+              // the FP32 value of z, as ranked by Sparsify (hi alone can be off by
+              // |A| 2^-24 when A and B cancel)
+              zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
+              // X~ below e^-87 at both points: no term of any sum changes
+              if (!(z0 > -87.0f) && !(zh > -87.0f)) continue;
+              // objective term X~ (expm1(t) - t) >= 0: FP32 suffices (no cancellation)
+              const float ef = exp2f(z0 * 1.4426950408889634f);
+              dfs = __fmaf_rn(ef, expm1_minus_x(tf), dfs);
+            } else {
+              zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
+              if (!(zh > -87.0f)) continue;   // dd_exp gives 0: nothing to add
             }
             const dd e = dd_exp(zh, zl, s_tab);
-            // the FP32 value of z, as ranked by Sparsify (hi alone can be off by
-            // |A| 2^-24 when A and B cancel)
-            zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
             dd_acc(racc, e.hi, e.lo);
             dd_acc(cdd[q], e.hi, e.lo);
           }

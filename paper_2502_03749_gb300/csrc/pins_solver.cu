@@ -73,6 +73,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.v = cv.take<double>(n);
   w.Add = cv.take<float2>(m); w.Bdd = cv.take<float2>(n);
   w.Ptdd = cv.take<float2>(m); w.Qtdd = cv.take<float2>(n);
+  w.A2dd = cv.take<float2>(m); w.B2dd = cv.take<float2>(n);
   w.mws.rowpart0 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart1 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart2 = cv.take<double>((size_t)g.gx * m);
@@ -95,6 +96,8 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.sw.cdata = cv.take<double>(kcap);
   w.sw.trow = cv.take<int>(kcap); w.sw.tval = cv.take<double>(kcap);
   w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
+  w.ent_row = cv.take<int>(2 * (size_t)kcap);
+  w.cg_u = cv.take<float>((size_t)N);
   w.cg_part = cv.take<double>(3 * 64 + 8);
   w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
   w.a = ip.ab ? cv.take<double>(m) : nullptr;
@@ -392,6 +395,10 @@ PassArgs Solver::args(double s, const double* F, const double* G) {
   a.F = F; a.G = G;
   a.A64 = ws_.A64; a.B64 = ws_.B64;
   a.Add = ws_.Add; a.Bdd = ws_.Bdd;
+  a.A2dd = ws_.A2dd; a.B2dd = ws_.B2dd;
+  const double k2 = kd * 1.4426950408889634074;
+  a.kappa2_dd.hi = (float)k2;
+  a.kappa2_dd.lo = (float)(k2 - (double)a.kappa2_dd.hi);
   a.a = a_; a.b = b_;
   a.exp_table = exp_table_;
   return a;
@@ -408,12 +415,21 @@ void Solver::prep(double s) {
 }
 
 void Solver::sinkhorn_iter(double s, int t) {
-  prep(s);
+  // the mixed passes read the log2-scaled pairs only; Add/Bdd are refreshed
+  // by the next prep() before any other pass
+  auto refresh = [&]() {
+    if (!mixed_) { prep(s); return; }
+    prof_begin(PC_VEC);
+    launch_prep2(ws_.F, ws_.G, m_, n_, eta_, s, ws_.A2dd, ws_.B2dd, stream_);
+    prof_end();
+    ++launches_;
+  };
+  refresh();
   PassArgs pa = args(s, ws_.F, ws_.G);
   prof_begin(PC_ROW_LSE);
   ps_->row_lse(pa, geom_, ws_.mws, ws_.F, ws_.scal + SC_ROWRES + t, stream_);
   prof_end();
-  prep(s);
+  refresh();
   prof_begin(PC_COL_LSE);
   ps_->col_lse(pa, geom_, ws_.mws, ws_.G, stream_);
   prof_end();
@@ -569,7 +585,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       int nnz = 0;
       if ((stt = sparsify(s, keep, zmax, &nnz)) != PINS_OK) { r.status = stt; return stt; }
       launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
-      cudaMemsetAsync(ws_.cg_part + 3 * 64, 0, sizeof(double), stream_);   // CG index-check flag
+      cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // CG index-check flag
       prof_begin(PC_CG);
       cudaError_t ce = run_cg(mixed_, m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
                               ws_.sw.data, ws_.grad, ws_.dir, cfg.cg_rtol, max_cg,
@@ -587,13 +603,15 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
                           mixed_ ? ws_.Qtdd : nullptr, stream_);
         ++launches_;
         marg(s, true);
-        cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL, 16 * sizeof(double),
+        // trial scalars, dot products, CG info and the CG index-check flag in one copy
+        cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL,
+                        (SC_FLAG + 1 - SC_TRIAL) * sizeof(double),
                         cudaMemcpyDeviceToHost, stream_);
         if ((stt = sync("line search")) != PINS_OK) { r.status = stt; return stt; }
         if (q == 0) {
           r.cg_iters += (int)h_scal_[SC_CG];
           int flag = 0;
-          cudaMemcpy(&flag, ws_.cg_part + 3 * 64, sizeof(int), cudaMemcpyDeviceToHost);
+          std::memcpy(&flag, h_scal_ + SC_FLAG, sizeof(int));
           if (flag) {
             err_ = "cg: an index outside the cluster's slices was skipped (flag " +
                    std::to_string(flag) + ")";
@@ -738,13 +756,14 @@ cudaError_t Solver::run_cg(bool mixed, int m, int n, double eta, const double* r
     bool used = false;
     cudaError_t ce = launch_pcg_dd(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
                                    ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.ent_tgt, ws_.ent_val,
+                                   ws_.ent_row, ws_.cg_u,
                                    rtol, max_iter, info,
-                                   reinterpret_cast<int*>(ws_.cg_part + 3 * 64), stream_, &used);
+                                   reinterpret_cast<int*>(ws_.scal + SC_FLAG), stream_, &used);
     if (used) return ce;
   }
   return launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr, ws_.sw.rowidx,
                     ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p, ws_.cg_q, ws_.cg_part, rtol,
-                    max_iter, info, sms_, stream_);
+                    max_iter, info, reinterpret_cast<int*>(ws_.scal + SC_FLAG), sms_, stream_);
 }
 
 pins_status Solver::step_cg(int m, int n, double eta, const double* r, const double* c,
@@ -756,7 +775,7 @@ pins_status Solver::step_cg(int m, int n, double eta, const double* r, const dou
   pins_status st = ensure(m, n, std::max(nnz, 1), 1, PINS_COST_GRID_SQEUCLID, false, false, 1);
   if (st != PINS_OK) return st;
   build_csc_from_csr(indptr, indices, data, m, n, nnz, ws_.sw, stream_);
-  cudaMemsetAsync(ws_.cg_part + 3 * 64, 0, sizeof(double), stream_);   // index-check flag
+  cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // index-check flag
   cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, rhs, d, rtol,
                           max_iter, info);
   launches_ += 5;

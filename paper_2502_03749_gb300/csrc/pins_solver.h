@@ -18,13 +18,14 @@ struct Workspace {
   double *F, *G, *Phi, *Psi, *A64, *B64, *r, *c, *rt, *ct, *Pt64, *Qt64;
   double *grad, *dir, *cg_res, *cg_p, *cg_q, *ab;
   double *xs, *u, *rr, *cr, *cp, *tc, *u2, *ys, *ec, *c1, *v;
-  float2 *Add, *Bdd, *Ptdd, *Qtdd;
+  float2 *Add, *Bdd, *Ptdd, *Qtdd, *A2dd, *B2dd;
   MergeWS mws;
   SparsifyState* st;
   unsigned int* hist;
   double* cand_key; long long* cand_idx;
   SparseWS sw;
-  int* ent_tgt; float2* ent_val;   // double-float CG: packed entries (2 kcap)
+  int* ent_tgt; float2* ent_val; int* ent_row;   // double-float CG: packed entries (2 kcap)
+  float* cg_u;                                  // double-float CG: u exchange (m + n)
   double* cg_part;
   double* scal;            // device scalars (see Solver::SC_*)
   // uploaded inputs
@@ -40,7 +41,7 @@ class Solver {
   // scalar slots in Workspace::scal (doubles)
   // (SC_STATE: 12 doubles of pinned host memory receive the SparsifyState)
   enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_STATE = 18,
-         SC_ROWRES = 32 };
+         SC_FLAG = 30, SC_ROWRES = 32 };
 
   Solver(int device, int sms, const float2* exp_table);
   ~Solver();

@@ -266,8 +266,8 @@ cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* 
                        const int* indptr, const int* indices, const double* data,
                        const int* colptr, const int* rowidx, const double* cdata,
                        const double* rhs, double* x, double* res, double* p, double* q,
-                       double* part, double rtol, int max_iter, double* info, int sms,
-                       cudaStream_t st) {
+                       double* part, double rtol, int max_iter, double* info, int* flag,
+                       int sms, cudaStream_t st) {
   CGArgs a;
   a.m = m; a.n = n; a.inv_eta = 1.0 / eta;
   a.r = r; a.c = c; a.indptr = indptr; a.indices = indices; a.data = data;
@@ -277,7 +277,7 @@ cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* 
   bool used = false;
   cudaError_t ce = launch_pcg_cluster(m, n, eta, r, c, indptr, indices, data, colptr, rowidx,
                                       cdata, rhs, x, rtol, max_iter, info,
-                                      reinterpret_cast<int*>(part + 3 * 64), st, &used);
+                                      flag, st, &used);
   if (used) return ce;
   const int N = m + n;
   a.dinv = q + N;   // (the cooperative path uses p globally; D^-1 goes after q)
@@ -304,6 +304,23 @@ void launch_prep(const double* F, const double* G, int m, int n, double eta, dou
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st) {
   int N = m + n; int blocks = (N + 255) / 256; if (blocks > 512) blocks = 512;
   k_prep<<<blocks, 256, 0, st>>>(F, G, m, n, 1.0 / eta, s, A64, B64, Add, Bdd);
+}
+
+// log2(e) A_i and log2(e) B_j as double-float pairs (mixed Sinkhorn passes)
+__global__ void k_prep2(const double* F, const double* G, int m, int n, double inv_eta,
+                        double s, float2* A2dd, float2* B2dd) {
+  const double L2E = 1.4426950408889634074;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += gridDim.x * blockDim.x) {
+    const double v = ((t < m) ? F[t] * inv_eta - s : G[t - m] * inv_eta) * L2E;
+    const float hi = __double2float_rn(v);
+    const float lo = __double2float_rn(v - (double)hi);
+    if (t < m) A2dd[t] = make_float2(hi, lo); else B2dd[t - m] = make_float2(hi, lo);
+  }
+}
+void launch_prep2(const double* F, const double* G, int m, int n, double eta, double s,
+                  float2* A2dd, float2* B2dd, cudaStream_t st) {
+  int N = m + n; int blocks = (N + 255) / 256; if (blocks > 512) blocks = 512;
+  k_prep2<<<blocks, 256, 0, st>>>(F, G, m, n, 1.0 / eta, s, A2dd, B2dd);
 }
 
 // trial increments Pt_i = alpha df_i / eta, Qt_j = alpha dg_j / eta

@@ -45,6 +45,31 @@ __device__ __forceinline__ typename KeyOf<P>::T rank_key(const PassArgs& p, int 
   }
 }
 
+// keys of entries (i, jb .. jb+3) on the mixed path, A = A_i; -inf past n
+template <class P>
+__device__ __forceinline__ void keys4_mixed(const PassArgs& p, float2 A, int i, int jb,
+                                            float k[4]) {
+  float c[4];
+  cost4<P>(p, i, jb, p.n, c);
+  float2 B[4];
+  if (jb + 3 < p.n) {
+    const float4 b01 = *reinterpret_cast<const float4*>(p.Bdd + jb);
+    const float4 b23 = *reinterpret_cast<const float4*>(p.Bdd + jb + 2);
+    B[0] = make_float2(b01.x, b01.y); B[1] = make_float2(b01.z, b01.w);
+    B[2] = make_float2(b23.x, b23.y); B[3] = make_float2(b23.z, b23.w);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) B[q] = (jb + q < p.n) ? p.Bdd[jb + q] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float wh, wl, zh, zl;
+    dd_w(B[q], c[q], p.kappa_dd.hi, p.kappa_dd.lo, wh, wl);
+    dd_z(A, wh, wl, zh, zl);
+    k[q] = (jb + q < p.n) ? __fadd_rn(zh, zl) : -INFINITY;
+  }
+}
+
 __device__ __forceinline__ int key_bin(double key, const SparsifyState& st) {
   double b = floor(__dmul_rn(__dsub_rn(__dsub_rn(st.kref, key), st.lo), st.inv_width));
   if (b < 0.0) return -1;
@@ -70,10 +95,24 @@ k_key_hist(PassArgs p, const SparsifyState* __restrict__ st_, unsigned int* hist
   const int lane = threadIdx.x & 31;
   const int wpb = PINS_TPB / 32;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < p.m; i += gridDim.x * wpb) {
+    if constexpr (P::MIXED) {
+      const float2 A = p.Add[i];
+#pragma unroll 2
+      for (int jb = 4 * lane; jb < p.n; jb += 128) {
+        float k[4];
+        keys4_mixed<P>(p, A, i, jb, k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int b = key_bin(k[q], st);
+          if (b >= 0 && b < PINS_HIST_NB) atomicAdd(&sh[b], 1u);
+        }
+      }
+    } else {
 #pragma unroll 8
-    for (int j = lane; j < p.n; j += 32) {
-      int b = key_bin(rank_key<P>(p, i, j), st);
-      if (b >= 0 && b < PINS_HIST_NB) atomicAdd(&sh[b], 1u);
+      for (int j = lane; j < p.n; j += 32) {
+        int b = key_bin(rank_key<P>(p, i, j), st);
+        if (b >= 0 && b < PINS_HIST_NB) atomicAdd(&sh[b], 1u);
+      }
     }
   }
   __syncthreads();
@@ -92,9 +131,7 @@ k_key_compact(PassArgs p, SparsifyState* st_, double* cand_key, long long* cand_
   const int wpb = PINS_TPB / 32;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < p.m; i += gridDim.x * wpb) {
     int above = 0;
-#pragma unroll 8
-    for (int j = lane; j < p.n; j += 32) {
-      auto k = rank_key<P>(p, i, j);
+    auto take = [&](auto k, int j) {
       int b = key_bin(k, st);
       above += (b < st.thr_bin) ? 1 : 0;
       if (b == st.thr_bin) {
@@ -102,6 +139,20 @@ k_key_compact(PassArgs p, SparsifyState* st_, double* cand_key, long long* cand_
         if (pos < PINS_CAND_CAP) { cand_key[pos] = (double)k; cand_idx[pos] = (long long)i * p.n + j; }
         else st_->overflow = 1;
       }
+    };
+    if constexpr (P::MIXED) {
+      const float2 A = p.Add[i];
+#pragma unroll 2
+      for (int jb = 4 * lane; jb < p.n; jb += 128) {
+        float k[4];
+        keys4_mixed<P>(p, A, i, jb, k);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (jb + q < p.n) take(k[q], jb + q);
+      }
+    } else {
+#pragma unroll 8
+      for (int j = lane; j < p.n; j += 32) take(rank_key<P>(p, i, j), j);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) above += __shfl_xor_sync(0xffffffffu, above, o);
@@ -119,6 +170,9 @@ k_key_write(PassArgs p, const SparsifyState* __restrict__ st_, const int* __rest
   const int lane = threadIdx.x & 31;
   const int wpb = PINS_TPB / 32;
   const unsigned int lt = (1u << lane) - 1u;
+  // tau in the key's own type (exact: it is one of the keys), so the per-entry
+  // test stays off the FP64 pipe on the mixed path
+  const typename KeyOf<P>::T tau = (typename KeyOf<P>::T)st.tau;
   for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < p.m; i += gridDim.x * wpb) {
     int pos = indptr[i];
     const int end = indptr[i + 1];
@@ -130,7 +184,7 @@ k_key_write(PassArgs p, const SparsifyState* __restrict__ st_, const int* __rest
       if (j < p.n) {
         k = rank_key<P>(p, i, j);
         const long long lin = (long long)i * p.n + j;
-        keep = ((double)k > st.tau) || ((double)k == st.tau && lin <= st.tau_idx);
+        keep = (k > tau) || (k == tau && lin <= st.tau_idx);
       }
       unsigned int bal = __ballot_sync(0xffffffffu, keep);
       if (keep) {
