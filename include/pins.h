@@ -107,6 +107,12 @@ typedef struct {
                                reserve; 0 = 80% of free memory at create time */
   int profile;          /* 1: time every kernel class of the blocking solver with
                            CUDA events (see pins_profile_read); 0 = off */
+  int sparsify_one_pass; /* mixed path: 1 (default) selects the kept entries of the
+                           later Newton steps of an outer iteration from the entries
+                           above the previous threshold minus an adaptive margin (one
+                           pass over C, exact top-K of the candidates); a failed
+                           selection is redone by the histogram search.  0 = always
+                           the histogram search.  The kept set is the same either way. */
 } pins_config;
 
 typedef struct {

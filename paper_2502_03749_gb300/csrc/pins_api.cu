@@ -97,6 +97,7 @@ extern "C" void pins_config_default(pins_config* c) {
   c->max_inflight = 4;
   c->queue_capacity = 4096;
   c->device_mem_budget = 0;
+  c->sparsify_one_pass = 1;
 }
 
 static bool config_ok(const pins_config& c, std::string& why) {

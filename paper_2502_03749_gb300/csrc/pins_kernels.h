@@ -9,6 +9,30 @@ struct SparsifyState;
 struct TrialArgs;
 struct CertArgs;
 
+// One-pass selection used between Newton steps of one outer iteration on the
+// mixed path: every entry whose key is at least tau_guess (the previous step's
+// threshold minus a margin) is collected; the exact top-K is then selected from
+// the candidates.  Lives in the solver's scalar block (4 doubles), so the host
+// reads it together with the line-search scalars.
+#define PINS_FAST_CAP 49152     // candidate capacity (keys staged in one CTA's shared memory)
+#define PINS_FAST_TIES 2048     // entries tied at the threshold key that can be ordered
+struct FastSelState {
+  unsigned int count;         // candidates found by the collect pass (may exceed the capacity)
+  unsigned int ncand;         // candidates used by the select pass (0 on failure)
+  int fail;                   // 1: fewer than K candidates, 2: too many, 3: too many ties
+  int pad;
+  float tau;                  // exact threshold key (FP32 key of the K-th entry)
+  float pad_f;
+  unsigned long long tie_max; // among keys equal to tau, keep packed (i, j) <= tie_max
+};
+
+// order-preserving map of FP32 keys to unsigned integers
+__device__ __forceinline__ unsigned int key_order(float x) {
+  const unsigned int b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+
 // One set of launchers per (precision policy, cost kind).
 struct PassSet {
   bool mixed;
@@ -26,6 +50,9 @@ struct PassSet {
                       int* rowcnt, int blocks, cudaStream_t);
   void (*key_write)(const PassArgs&, const SparsifyState*, const int* indptr, int* indices,
                     double* data, int blocks, cudaStream_t);
+  // one-pass candidate collection (mixed policy only; nullptr otherwise)
+  void (*fast_collect)(const PassArgs&, float tau_guess, FastSelState*, float* ckey,
+                       unsigned long long* cij, int blocks, cudaStream_t);
 };
 
 const PassSet* passes_f64(int kind);
@@ -38,10 +65,17 @@ struct SparseWS {
   int* indptr; int* indices; double* data;    // CSR: m+1, cap, cap
   int* colptr; int* rowidx; double* cdata;    // CSC: n+1, cap, cap
   int* trow; double* tval;       // CSC placement before the per-column sort: cap, cap
+  int* tcol; double* tcval;      // CSR placement before the per-row sort (one-pass selection)
 };
 void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
                         int nnz, const SparseWS& sw, cudaStream_t st);
 void launch_scan(int* cnt, int* ptr, int len, cudaStream_t st);
+// CSR + CSC of the entries kept by the one-pass selection (no-op when it failed)
+void build_sparse_from_candidates(const FastSelState* fs, const float* ckey,
+                                  const unsigned long long* cij, int m, int n, int keep,
+                                  const SparseWS& sw, cudaStream_t st);
+cudaError_t launch_fast_select(FastSelState* fs, const float* ckey, const unsigned long long* cij,
+                               int K, cudaStream_t s);
 cudaError_t launch_pcg(int m, int n, double eta, const double* r, const double* c,
                        const int* indptr, const int* indices, const double* data,
                        const int* colptr, const int* rowidx, const double* cdata,

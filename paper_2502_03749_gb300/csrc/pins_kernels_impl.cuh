@@ -106,9 +106,14 @@ template <int K> struct Launch {
                         double* data, int blocks, cudaStream_t st) {
     k_key_write<P><<<blocks, PINS_TPB, 0, st>>>(p, s, indptr, indices, data);
   }
+  static void fast_collect(const PassArgs& p, float tau_guess, FastSelState* fs, float* ckey,
+                           unsigned long long* cij, int blocks, cudaStream_t st) {
+    if constexpr (P::MIXED)
+      k_fast_collect<P><<<blocks, PINS_TPB, 0, st>>>(p, tau_guess, fs, ckey, cij);
+  }
   static const PassSet* get() {
     static const PassSet ps = {P::MIXED, row_lse, col_lse, marg, cert, key_hist, key_compact,
-                               key_write};
+                               key_write, P::MIXED ? fast_collect : nullptr};
     return &ps;
   }
 };

@@ -120,4 +120,132 @@ cudaError_t launch_cand_select(SparsifyState* st, const double* cand_key,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------- //
+// Exact top-K of the one-pass candidates (one CTA, 1024 threads).  Keys are
+// mapped to order-preserving unsigned integers and the K-th largest is found by
+// a three-pass radix select (11, 11, 10 bits) over the keys staged in shared
+// memory; the entries tied at that key are then ordered by packed (i, j) and the
+// first `need` kept, exactly as the histogram path ranks (key desc, index asc).
+// Resets fs->count for the next collect pass.
+// ------------------------------------------------------------------------- //
+__global__ void __launch_bounds__(1024)
+k_fast_select(FastSelState* fs, const float* ckey, const unsigned long long* cij, int K) {
+  extern __shared__ unsigned int fsm[];
+  unsigned int* su = fsm;                                  // PINS_FAST_CAP keys
+  unsigned int* hist = su + PINS_FAST_CAP;                 // 2048 bins
+  unsigned long long* tie = reinterpret_cast<unsigned long long*>(hist + 2048);  // PINS_FAST_TIES
+  __shared__ unsigned int s_digit, s_want, s_nt;
+  const int t = threadIdx.x;
+  const unsigned int cnt = fs->count;
+  __syncthreads();
+  if (t == 0) fs->count = 0u;
+  if (cnt < (unsigned int)K || cnt > PINS_FAST_CAP) {
+    if (t == 0) { fs->fail = (cnt < (unsigned int)K) ? 1 : 2; fs->ncand = 0u; }
+    return;
+  }
+  for (unsigned int q = t; q < cnt; q += 1024) su[q] = key_order(ckey[q]);
+  unsigned int prefix = 0u, pmask = 0u, want = (unsigned int)K;
+  const int shifts[3] = {21, 10, 0};
+  const int widths[3] = {11, 11, 10};
+  for (int ps = 0; ps < 3; ++ps) {
+    const int sh = shifts[ps];
+    const unsigned int nb = 1u << widths[ps];
+    for (unsigned int b = t; b < 2048u; b += 1024) hist[b] = 0u;
+    if (t == 0) s_digit = 0xffffffffu;
+    __syncthreads();
+    for (unsigned int q = t; q < cnt; q += 1024) {
+      const unsigned int u = su[q];
+      if ((u & pmask) == prefix) atomicAdd(&hist[(u >> sh) & (nb - 1u)], 1u);
+    }
+    __syncthreads();
+    if (t < 32) {
+      // digits from the top: the first (highest) digit whose cumulative count reaches want
+      const unsigned int per = nb / 32u;                   // bins per lane, lane 0 = top bins
+      unsigned int loc = 0u;
+      for (unsigned int b = 0; b < per; ++b) loc += hist[nb - 1u - (t * per + b)];
+      unsigned int inc = loc;                              // inclusive scan over lanes
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (t >= o) inc += v;
+      }
+      const unsigned int excl = inc - loc;
+      const unsigned int hitmask = __ballot_sync(0xffffffffu, excl < want && inc >= want);
+      const int owner = __ffs(hitmask) - 1;
+      if (t == owner) {
+        unsigned int run = excl;
+        for (unsigned int b = 0; b < per; ++b) {
+          const unsigned int bin = nb - 1u - (t * per + b);
+          const unsigned int h = hist[bin];
+          if (run + h >= want) { s_digit = bin; s_want = want - run; break; }
+          run += h;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_digit == 0xffffffffu) {                          // counts inconsistent with K
+      if (t == 0) { fs->fail = 4; fs->ncand = 0u; }
+      return;
+    }
+    prefix |= s_digit << sh;
+    pmask |= (nb - 1u) << sh;
+    want = s_want;
+    __syncthreads();
+  }
+  // prefix is the threshold key; `want` entries are needed among the ties
+  if (t == 0) s_nt = 0u;
+  __syncthreads();
+  for (unsigned int q = t; q < cnt; q += 1024) {
+    if (su[q] == prefix) {
+      const unsigned int pos = atomicAdd(&s_nt, 1u);
+      if (pos < PINS_FAST_TIES) tie[pos] = cij[q];
+    }
+  }
+  __syncthreads();
+  const unsigned int nt = s_nt;
+  if (nt > PINS_FAST_TIES || nt < want) {
+    if (t == 0) { fs->fail = 3; fs->ncand = 0u; }
+    return;
+  }
+  unsigned int P2 = 1u;
+  while (P2 < nt) P2 <<= 1;
+  for (unsigned int q = nt + t; q < P2; q += 1024) tie[q] = ~0ull;
+  __syncthreads();
+  for (unsigned int k = 2; k <= P2; k <<= 1) {
+    for (unsigned int jv = k >> 1; jv > 0; jv >>= 1) {
+      for (unsigned int q = t; q < P2; q += 1024) {
+        const unsigned int l = q ^ jv;
+        if (l > q) {
+          const bool up = (q & k) == 0;
+          const unsigned long long a = tie[q], b = tie[l];
+          if (up ? (a > b) : (a < b)) { tie[q] = b; tie[l] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (t == 0) {
+    const unsigned int u = prefix;
+    const unsigned int bits = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    fs->tau = __uint_as_float(bits);
+    fs->tie_max = tie[want - 1u];
+    fs->ncand = cnt;
+    fs->fail = 0;
+  }
+}
+
+cudaError_t launch_fast_select(FastSelState* fs, const float* ckey, const unsigned long long* cij,
+                               int K, cudaStream_t s) {
+  const size_t smem = sizeof(unsigned int) * (PINS_FAST_CAP + 2048) +
+                      sizeof(unsigned long long) * PINS_FAST_TIES;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_fast_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k_fast_select<<<1, 1024, smem, s>>>(fs, ckey, cij, K);
+  return cudaGetLastError();
+}
+
 }  // namespace pins

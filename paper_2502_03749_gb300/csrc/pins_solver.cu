@@ -95,6 +95,8 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.sw.colptr = cv.take<int>(n + 1); w.sw.rowidx = cv.take<int>(kcap);
   w.sw.cdata = cv.take<double>(kcap);
   w.sw.trow = cv.take<int>(kcap); w.sw.tval = cv.take<double>(kcap);
+  w.sw.tcol = cv.take<int>(kcap); w.sw.tcval = cv.take<double>(kcap);
+  w.fkey = cv.take<float>(PINS_FAST_CAP); w.fij = cv.take<unsigned long long>(PINS_FAST_CAP);
   w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
   w.ent_row = cv.take<int>(2 * (size_t)kcap);
   w.cg_u = cv.take<float>((size_t)N);
@@ -511,6 +513,22 @@ pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out) {
   return check("csr");
 }
 
+void Solver::sparsify_fast(double s, int keep, float tau_guess) {
+  FastSelState* fs = reinterpret_cast<FastSelState*>(ws_.scal + SC_FAST);
+  PassArgs pa = args(s, ws_.F, ws_.G);
+  const int blocks = std::min(std::max((m_ + 7) / 8, 1), sms_ * 8);
+  prof_begin(PC_COMPACT);
+  ps_->fast_collect(pa, tau_guess, fs, ws_.fkey, ws_.fij, blocks, stream_);
+  prof_end();
+  prof_begin(PC_SELECT);
+  launch_fast_select(fs, ws_.fkey, ws_.fij, keep, stream_);
+  prof_end();
+  prof_begin(PC_WRITE);
+  build_sparse_from_candidates(fs, ws_.fkey, ws_.fij, m_, n_, keep, ws_.sw, stream_);
+  prof_end();
+  launches_ += 6;
+}
+
 pins_status Solver::certificate(double s) {
   launch_cert_pre(a_, ws_.r, ws_.F, m_, s, eta_, ws_.xs, ws_.u, stream_);
   prep(s);
@@ -551,6 +569,11 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
   cudaMemsetAsync(ws_.Psi, 0, sizeof(double) * n, stream_);
   cudaMemcpyAsync(ws_.ab, a_, sizeof(double) * m, cudaMemcpyDeviceToDevice, stream_);
   cudaMemcpyAsync(ws_.ab + m, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream_);
+  cudaMemsetAsync(ws_.scal + SC_FAST, 0, sizeof(FastSelState), stream_);
+  // one-pass selection between the Newton steps of an outer iteration (mixed path)
+  const bool fast_path = mixed_ && cfg.sparsify_one_pass != 0 && ps_->fast_collect != nullptr &&
+                         2 * keep <= PINS_FAST_CAP;
+  float fast_margin = 1.0f;
   int outer = 0;
   bool stop = false, cert_current = false;
   double res = INFINITY, zmax = 0.0;
@@ -580,10 +603,21 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
     res = h_scal_[SC_MARG + 0];
     zmax = h_scal_[SC_MARG + 2];
     int steps = 0;
+    bool fast_ok = false;      // this outer iteration has a CSR/CSC and an exact threshold
+    float tau_prev = 0.f;
     while (steps < cfg.T2) {
       if (!(res > tol)) break;
       int nnz = 0;
-      if ((stt = sparsify(s, keep, zmax, &nnz)) != PINS_OK) { r.status = stt; return stt; }
+      const bool fast = fast_path && fast_ok;
+      if (fast) {
+        // candidates above the previous threshold minus a margin; a failed
+        // selection leaves the previous CSR/CSC and is redone below
+        sparsify_fast(s, keep, tau_prev - fast_margin);
+      } else {
+        if ((stt = sparsify(s, keep, zmax, &nnz)) != PINS_OK) { r.status = stt; return stt; }
+        tau_prev = (float)reinterpret_cast<const SparsifyState*>(h_scal_ + SC_STATE)->tau;
+        fast_ok = fast_path;
+      }
       launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
       cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // CG index-check flag
       prof_begin(PC_CG);
@@ -594,7 +628,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
       launch_dot2(ws_.grad, ws_.dir, ws_.ab, ws_.dir, m + n, ws_.scal + SC_DOTS, stream_);
       launches_ += 3;
-      bool accepted = false;
+      bool accepted = false, redo = false;
       double alpha = 1.0;
       int q = 0;
       for (; q <= cfg.max_backtrack; ++q) {
@@ -603,11 +637,27 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
                           mixed_ ? ws_.Qtdd : nullptr, stream_);
         ++launches_;
         marg(s, true);
-        // trial scalars, dot products, CG info and the CG index-check flag in one copy
+        // trial scalars, dot products, CG info, the CG index-check flag and the
+        // one-pass selection state in one copy
         cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL,
-                        (SC_FLAG + 1 - SC_TRIAL) * sizeof(double),
+                        (SC_FAST + 4 - SC_TRIAL) * sizeof(double),
                         cudaMemcpyDeviceToHost, stream_);
         if ((stt = sync("line search")) != PINS_OK) { r.status = stt; return stt; }
+        if (q == 0 && fast) {
+          FastSelState f;
+          std::memcpy(&f, h_scal_ + SC_FAST, sizeof(f));
+          if (f.fail) {
+            // too few (1) or too many (2) candidates: widen or narrow the margin;
+            // too many ties (3) or inconsistent counts: the histogram path
+            if (f.fail == 1) fast_margin = std::min(64.0f, 2.0f * fast_margin);
+            else if (f.fail == 2) fast_margin = std::max(1e-3f, 0.5f * fast_margin);
+            redo = true;
+            break;
+          }
+          tau_prev = f.tau;
+          if (f.ncand > 3u * (unsigned)keep) fast_margin = std::max(1e-3f, 0.7f * fast_margin);
+          else if (f.ncand < (unsigned)keep + keep / 4) fast_margin = std::min(64.0f, 1.4f * fast_margin);
+        }
         if (q == 0) {
           r.cg_iters += (int)h_scal_[SC_CG];
           int flag = 0;
@@ -627,6 +677,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         if (std::isfinite(dP) && dP >= cfg.armijo_c1 * alpha * gtd) { accepted = true; break; }
         alpha *= cfg.armijo_beta;
       }
+      if (redo) { fast_ok = false; continue; }   // same step again, histogram path
       r.ls_trials += std::min(q + 1, cfg.max_backtrack + 1);
       ++steps;
       if (accepted) {

@@ -25,6 +25,7 @@ struct Workspace {
   double* cand_key; long long* cand_idx;
   SparseWS sw;
   int* ent_tgt; float2* ent_val; int* ent_row;   // double-float CG: packed entries (2 kcap)
+  float* fkey; unsigned long long* fij;          // one-pass selection candidates
   float* cg_u;                                  // double-float CG: u exchange (m + n)
   double* cg_part;
   double* scal;            // device scalars (see Solver::SC_*)
@@ -41,7 +42,7 @@ class Solver {
   // scalar slots in Workspace::scal (doubles)
   // (SC_STATE: 12 doubles of pinned host memory receive the SparsifyState)
   enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_STATE = 18,
-         SC_FLAG = 30, SC_ROWRES = 32 };
+         SC_FLAG = 30, SC_FAST = 32, SC_ROWRES = 40 };
 
   Solver(int device, int sms, const float2* exp_table);
   ~Solver();
@@ -111,6 +112,9 @@ class Solver {
   void sinkhorn_iter(double s, int t);
   void marg(double s, bool trial);
   pins_status sparsify(double s, int keep, double zmax, int* nnz_out);
+  // one-pass selection for the later Newton steps of an outer iteration (mixed);
+  // launches only, the outcome is read at the next line-search sync
+  void sparsify_fast(double s, int keep, float tau_guess);
   pins_status certificate(double s);
   PassArgs args(double s, const double* F, const double* G);
 

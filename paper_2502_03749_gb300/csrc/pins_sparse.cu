@@ -72,12 +72,12 @@ __global__ void k_csc_place(const int* indptr, const int* indices, const double*
       tval[pos] = data[e];
     }
 }
-__global__ void k_csc_segsort(const int* colptr, int n, int* fill, const int* trow,
-                              const double* tval, int* rowidx, double* cdata) {
+// one warp sorts segment j of (tkey, tval) by key into (okey, oval); fill[j] = 0
+__device__ __forceinline__ void warp_seg_sort(int j, const int* ptr, int* fill, const int* trow,
+                                              const double* tval, int* rowidx, double* cdata) {
   const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw) {
-    const int b = colptr[j], len = colptr[j + 1] - b;
+  {
+    const int b = ptr[j], len = ptr[j + 1] - b;
     if (lane == 0) fill[j] = 0;
     if (len <= 32) {
       int r = (lane < len) ? trow[b + lane] : 0x7fffffff;
@@ -107,6 +107,114 @@ __global__ void k_csc_segsort(const int* colptr, int n, int* fill, const int* tr
       }
     }
   }
+}
+__global__ void k_csc_segsort(const int* colptr, int n, int* fill, const int* trow,
+                              const double* tval, int* rowidx, double* cdata) {
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw)
+    warp_seg_sort(j, colptr, fill, trow, tval, rowidx, cdata);
+}
+
+// ------------------------------------------------------------------------- //
+// CSR and CSC of the entries kept by the one-pass selection (FastSelState):
+// counts per row and column, both scans, atomic placement, then a warp per row
+// (by column) and per column (by row) sorts its segment.  Every kernel does
+// nothing when the selection failed, so the previous CSR/CSC stay intact.
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ bool fast_kept(const FastSelState& f, float key, unsigned long long ij) {
+  const unsigned int u = key_order(key), T = key_order(f.tau);
+  return u > T || (u == T && ij <= f.tie_max);
+}
+__global__ void k_fast_count(const FastSelState* fs, const float* ckey,
+                             const unsigned long long* cij, int* rowcnt, int* colcnt) {
+  const FastSelState f = *fs;
+  if (f.fail) return;
+  for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < f.ncand; q += gridDim.x * blockDim.x) {
+    const unsigned long long ij = cij[q];
+    if (fast_kept(f, ckey[q], ij)) {
+      atomicAdd(rowcnt + (int)(ij >> 32), 1);
+      atomicAdd(colcnt + (int)(ij & 0xffffffffu), 1);
+    }
+  }
+}
+// CTA 0 scans the row counts, CTA 1 the column counts (each as k_scan)
+__global__ void __launch_bounds__(1024) k_scan2(const FastSelState* fs, int* c0, int* p0, int l0,
+                                                int* c1, int* p1, int l1) {
+  if (fs->fail) return;
+  __shared__ int wsum[32];
+  int* cnt = blockIdx.x ? c1 : c0;
+  int* ptr = blockIdx.x ? p1 : p0;
+  const int len = blockIdx.x ? l1 : l0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (len + 1023) / 1024;
+  const int b0 = min(len, tid * per), b1 = min(len, b0 + per);
+  int tot = 0;
+  for (int t = b0; t < b1; ++t) tot += cnt[t];
+  int inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += v;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  int run = inc - tot + (warp > 0 ? wsum[warp - 1] : 0);
+  for (int t = b0; t < b1; ++t) { const int v = cnt[t]; ptr[t] = run; run += v; cnt[t] = 0; }
+  if (tid == 1023) ptr[len] = wsum[31];
+}
+__global__ void k_fast_place(const FastSelState* fs, const float* ckey,
+                             const unsigned long long* cij, const int* indptr, int* rowfill,
+                             int* tcol, double* tcval, const int* colptr, int* colfill, int* trow,
+                             double* tval) {
+  const FastSelState f = *fs;
+  if (f.fail) return;
+  for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < f.ncand; q += gridDim.x * blockDim.x) {
+    const unsigned long long ij = cij[q];
+    const float key = ckey[q];
+    if (!fast_kept(f, key, ij)) continue;
+    const int i = (int)(ij >> 32), j = (int)(ij & 0xffffffffu);
+    const double v = exp((double)key);              // X~_ij from its FP32 log (mixed path)
+    const int pr = indptr[i] + atomicAdd(rowfill + i, 1);
+    tcol[pr] = j; tcval[pr] = v;
+    const int pc = colptr[j] + atomicAdd(colfill + j, 1);
+    trow[pc] = i; tval[pc] = v;
+  }
+}
+__global__ void k_fast_segsort(const FastSelState* fs, int m, int n, const int* indptr,
+                               int* rowfill, const int* tcol, const double* tcval, int* indices,
+                               double* data, const int* colptr, int* colfill, const int* trow,
+                               const double* tval, int* rowidx, double* cdata) {
+  if (fs->fail) return;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < m + n; s += nw) {
+    if (s < m) warp_seg_sort(s, indptr, rowfill, tcol, tcval, indices, data);
+    else warp_seg_sort(s - m, colptr, colfill, trow, tval, rowidx, cdata);
+  }
+}
+
+void build_sparse_from_candidates(const FastSelState* fs, const float* ckey,
+                                  const unsigned long long* cij, int m, int n, int keep,
+                                  const SparseWS& sw, cudaStream_t st) {
+  const int cb = std::max(1, std::min((PINS_FAST_CAP + 255) / 256, 192));
+  k_fast_count<<<cb, 256, 0, st>>>(fs, ckey, cij, sw.rowcnt, sw.colcnt);
+  k_scan2<<<2, 1024, 0, st>>>(fs, sw.rowcnt, sw.indptr, m, sw.colcnt, sw.colptr, n);
+  k_fast_place<<<cb, 256, 0, st>>>(fs, ckey, cij, sw.indptr, sw.rowcnt, sw.tcol, sw.tcval,
+                                   sw.colptr, sw.colcnt, sw.trow, sw.tval);
+  const int sb = std::max(1, std::min((m + n + 7) / 8, 2368));
+  k_fast_segsort<<<sb, 256, 0, st>>>(fs, m, n, sw.indptr, sw.rowcnt, sw.tcol, sw.tcval,
+                                     sw.indices, sw.data, sw.colptr, sw.colcnt, sw.trow, sw.tval,
+                                     sw.rowidx, sw.cdata);
+  (void)keep;
 }
 
 void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,

@@ -1,6 +1,7 @@
 // Sparsify kernels of PINS (threshold selection and ordered CSR output).
 #pragma once
 #include "pins_passes.cuh"
+#include "pins_kernels.h"
 
 namespace pins {
 
@@ -198,4 +199,38 @@ k_key_write(PassArgs p, const SparsifyState* __restrict__ st_, const int* __rest
     }
   }
 }
+// candidates of the one-pass selection: keys >= tau_guess, with packed (i, j)
+template <class P>
+__global__ void __launch_bounds__(PINS_TPB)
+k_fast_collect(PassArgs p, float tg, FastSelState* fs, float* ckey, unsigned long long* cij) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = PINS_TPB / 32;
+  const unsigned int lt = (1u << lane) - 1u;
+  for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < p.m; i += gridDim.x * wpb) {
+    const float2 A = p.Add[i];
+#pragma unroll 2
+    for (int jb = 4 * lane; jb < p.n; jb += 128) {
+      float k[4];
+      keys4_mixed<P>(p, A, i, jb, k);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool keep = k[q] >= tg;            // -inf past n never passes
+        const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+        if (bal) {
+          unsigned int base = 0;
+          if (lane == 0) base = atomicAdd(&fs->count, (unsigned int)__popc(bal));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (keep) {
+            const unsigned int pos = base + __popc(bal & lt);
+            if (pos < PINS_FAST_CAP) {
+              ckey[pos] = k[q];
+              cij[pos] = ((unsigned long long)(unsigned int)i << 32) | (unsigned int)(jb + q);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 }  // namespace pins

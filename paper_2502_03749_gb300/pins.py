@@ -52,7 +52,7 @@ class pins_config(ct.Structure):
                 ("gap_every", ct.c_int), ("prec", ct.c_int), ("device", ct.c_int),
                 ("cuda_stream", ct.c_void_p), ("max_inflight", ct.c_int),
                 ("queue_capacity", ct.c_int), ("device_mem_budget", ct.c_size_t),
-                ("profile", ct.c_int)]
+                ("profile", ct.c_int), ("sparsify_one_pass", ct.c_int)]
 
 
 class pins_problem(ct.Structure):

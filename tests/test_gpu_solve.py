@@ -138,6 +138,30 @@ def test_batch_and_serving_match_solo(prec):
         assert np.array_equal(s["F"], b["F"]) and np.array_equal(s["F"], v["F"])
 
 
+@pytest.mark.parametrize("case", ["gmm", "grid"])
+def test_one_pass_selection_matches_histogram_search(case):
+    """The mixed path's one-pass selection (later Newton steps of an outer
+    iteration) keeps exactly the entries the histogram search keeps, so the two
+    give bit-identical solves.  The grid case has many tied keys."""
+    if case == "gmm":
+        w = wl.gmm_instance(0, m=300, n=280, eta=1e-2)
+    else:
+        w = wl.grid_instance(16, 0, eta=1e-2)
+    ref = pins.problem_from_workload(w)
+    out = []
+    for one_pass in (1, 0):
+        h = pins.Pins(prec="mixed", eta=1e-2, K=4, sparsify_one_pass=one_pass)
+        try:
+            out.append(h.solve(ref))
+        finally:
+            h.close()
+    a, b = out
+    assert a["newton_iters"] == b["newton_iters"] and a["cg_iters"] == b["cg_iters"]
+    assert a["cost"] == b["cost"]
+    assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["G"], b["G"])
+    assert a["newton_iters"] > 4        # the one-pass path ran (steps after the first)
+
+
 def test_invalid_inputs_rejected():
     rng = np.random.default_rng(1)
     C = rng.uniform(size=(5, 6))
