@@ -108,6 +108,17 @@ MN_CLASSES = ("row_lse", "col_lse", "marginals", "trial", "key_hist", "key_compa
               "csr_write", "certificate")
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure is measured by the driver)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 units x clock, FMA = 2 flops
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
+# each class's kernel on this workload (mid-solve, caches flushed by ncu); the
+# summaries with their commands are in profiles/.  Set a class to None when its
+# kernel changes until it is captured again.
+NCU_TRAFFIC_BYTES = {
+    "cg": 426240,            # k_pcg_dd            (profiles/k_pcg_dd_gmm4096.md)
+    "trial": 67693824,       # k_marg_mx<mixed,1>  (profiles/k_marg_mx_trial_gmm4096.md)
+    "row_lse": 67636736,     # k_row_lse_mx        (profiles/sinkhorn_lse_mx_gmm4096.md)
+    "col_lse": 67527168,     # k_col_lse_mx        (profiles/sinkhorn_lse_mx_gmm4096.md)
+    "key_compact": 67311360, # k_fast_collect      (profiles/sparsify_one_pass_gmm4096.md)
+}
 
 
 def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, mixed):
@@ -218,7 +229,7 @@ def cpu_baseline_sample(args, w):
     C, a, b = w.dense_cost(), w.a, w.b
     F, G = np.zeros(args.n), np.zeros(args.n)
     iters, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < args.cpu_seconds:
+    while iters == 0 or time.perf_counter() - t0 < args.cpu_seconds:
         F, _ = po.sinkhorn_row_step(C, a, F, G, args.eta, 1.0)
         G = po.sinkhorn_col_step(C, b, F, G, args.eta, 1.0)
         iters += 1
@@ -359,6 +370,10 @@ def run_ours(args):
     roof, dom = roofline(prof, args.n, args.n, 4 if args.prec == "mixed" else 8, prof_cg_iters,
                          keep, peaks, args.prec == "mixed")
     if roof is not None:
+        if args.prec == "mixed" and args.n == 4096:
+            roof["traffic"] = NCU_TRAFFIC_BYTES.get(dom)
+            if roof["traffic"] is not None:
+                roof["traffic_unit"] = "bytes per launch (ncu, cold caches)"
         roof["timing"] = ("CUDA events on the solver's stream around every launch, one profiled "
                           "solve after the timed region")
     line["roofline"] = roof
