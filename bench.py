@@ -44,6 +44,20 @@ def parse():
     return ap.parse_args()
 
 
+def whole_job_rate(t_local: float, steps: int, world: int, device: str = "cpu"):
+    """Max over ranks of the timed-region length, and the whole-job rate (every
+    rank ran `steps` independent solves).  Needs an initialised process group when
+    world > 1 (NCCL with device='cuda' in the benchmark, gloo with 'cpu' in tests)."""
+    t = float(t_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return steps * world / t, t
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -292,12 +306,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
-    value = args.steps * world / t
+    value, t = whole_job_rate(ev0.elapsed_time(ev1) / 1e3, args.steps, world, device="cuda")
     # e2e: host pinned inputs -> public API -> potentials back, every step
     hp = {"C": torch.from_numpy(C32).pin_memory(), "a": torch.from_numpy(w.a).pin_memory(),
           "b": torch.from_numpy(w.b).pin_memory()}

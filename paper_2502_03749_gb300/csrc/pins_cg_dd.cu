@@ -45,6 +45,8 @@ struct CGddArgs {
   const int* indptr; const int* indices; const double* data;
   const int* colptr; const int* rowidx; const double* cdata;
   const double* rhs; double* x;
+  const double* ab;                // (a; b): with rhs == NULL, rhs = (a - r; b - c)
+  double* dots;                    // if not NULL: <rhs, x> and <ab, x> (FP64, fixed order)
   int* ent_tgt; float2* ent_val;   // scratch: one slot per entry of the CSR + CSC entry space
   int* ent_row;
   float* ug;                       // u of every unknown (N floats), the exchange buffer
@@ -53,63 +55,13 @@ struct CGddArgs {
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
 };
 
-// FP64 -> double-float with integer operations only: hi = the sign, exponent and
-// top 23 stored significand bits (truncated), lo = the remaining 29 bits rounded
-// to FP32, so hi + lo carries ~48 significand bits.  The binary exponent is
-// lowered by `shift` (an exact scaling by 2^-shift).  Zero, FP64 subnormals and
-// scaled magnitudes below 2^-126 give 0; above 2^128 give inf; NaN stays NaN.
-__device__ __forceinline__ float2 split_f64(double v, int shift) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ffu);
-  const unsigned long long mant = b & 0xfffffffffffffull;
-  if (e == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.f);
-  const int fe = e - 1023 + 127 - shift;
-  if (e == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
-  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
-  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
-  const unsigned rest = (unsigned)(mant & 0x1fffffffu);
-  // rest * 2^-52 is exact and normal; times 2^(fe - 127) may round if subnormal
-  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(rest), 0x1p-52f), __uint_as_float((unsigned)fe << 23));
-  if (sign) lo = -lo;
-  return make_float2(hi, lo);
-}
-
-__device__ __forceinline__ float2 ddv_mul(float2 a, float2 b) {
-  float p, e; two_prod(a.x, b.x, p, e);
-  e = __fmaf_rn(a.x, b.y, e);
-  e = __fmaf_rn(a.y, b.x, e);
-  float h, l; fast_two_sum(p, e, h, l);
-  return make_float2(h, l);
-}
-// y + f * v  (f FP32, v and y double-float), normalised
-__device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
-  float p, e; two_prod(f, v.x, p, e);
-  e = __fmaf_rn(f, v.y, e);
-  float s, t; two_sum(y.x, p, s, t);
-  t = __fadd_rn(t, __fadd_rn(y.y, e));
-  float h, l; fast_two_sum(s, t, h, l);
-  return make_float2(h, l);
-}
-// acc += v * u (v double-float, u FP32), unnormalised accumulation
-__device__ __forceinline__ void ddv_acc_mul(float2& acc, float2 v, float u) {
-  float p, e; two_prod(v.x, u, p, e);
-  e = __fmaf_rn(v.y, u, e);
-  float s, t; two_sum(acc.x, p, s, t);
-  acc.x = s; acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
-}
-__device__ __forceinline__ float2 ddv_add(float2 a, float2 b) {
-  float s, t; two_sum(a.x, b.x, s, t);
-  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
-  float h, l; fast_two_sum(s, t, h, l);
-  return make_float2(h, l);
-}
-
 __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
   __shared__ float slot[3 * PINS_DDCG_MAX];
   __shared__ unsigned int eslot[1];
+  __shared__ double dred[2][PINS_DDCG_TPB / 32];
+  __shared__ double dslot[2][PINS_DDCG_MAX];
   __shared__ float red[3][PINS_DDCG_TPB / 32];
   __shared__ unsigned int ered[PINS_DDCG_TPB / 32];
   __shared__ int hrow[PINS_DDCG_TPB];
@@ -142,11 +94,16 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     return (t < m) ? __ldg(a.indptr + t) : Kc + __ldg(a.colptr + t - m);
   };
   const float2 ie = split_f64(a.inv_eta, 0);
+  // the right-hand side: given, or the gradient (a - r; b - c) of the Newton step
+  auto rhs_of = [&](int t) -> double {
+    if (a.rhs) return a.rhs[t];
+    return a.ab[t] - ((t < m) ? __ldg(a.r + t) : __ldg(a.c + t - m));
+  };
 
   // ---- scale: largest binary exponent of rhs over the cluster ----
   unsigned int emax = 0u;
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(a.rhs[lo + k]);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(rhs_of(lo + k));
     emax = max(emax, (unsigned)((b >> 52) & 0x7ffu));
   }
   emax = __reduce_max_sync(0xffffffffu, emax);
@@ -205,7 +162,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   const int shift = (int)E - 1023;                  // max |rhs| 2^-shift in [1, 2)
   float lr = 0.f;
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-    const float2 r0 = split_f64(a.rhs[lo + k], shift);
+    const float2 r0 = split_f64(rhs_of(lo + k), shift);
     rv[k] = r0;
     u[k] = __fmul_rn(dinv[k], r0.x);
     __stcg(a.ug + lo + k, u[k]);
@@ -409,13 +366,39 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     gam = gn;
   }
   const double scale = ldexp(1.0, shift);
-  for (int k = tid; k < nl; k += PINS_DDCG_TPB)
-    a.x[lo + k] = ((double)xv[k].x + (double)xv[k].y) * scale;
+  double dg0 = 0.0, dg1 = 0.0;                      // <rhs, x>, <ab, x> partials
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    const double xk = ((double)xv[k].x + (double)xv[k].y) * scale;
+    a.x[lo + k] = xk;
+    if (a.dots) { dg0 += rhs_of(lo + k) * xk; dg1 += a.ab[lo + k] * xk; }
+  }
+  if (a.dots) {   // block sums in a fixed tree, then rank 0 adds the CTAs in rank order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dg0 += __shfl_xor_sync(0xffffffffu, dg0, o);
+      dg1 += __shfl_xor_sync(0xffffffffu, dg1, o);
+    }
+    if (lane == 0) { dred[0][warp] = dg0; dred[1][warp] = dg1; }
+    __syncthreads();
+    if (tid == 0) {
+      double b0 = 0.0, b1 = 0.0;
+      for (int w = 0; w < PINS_DDCG_TPB / 32; ++w) { b0 += dred[0][w]; b1 += dred[1][w]; }
+      double* rs = cluster.map_shared_rank(&dslot[0][0], 0);
+      rs[rank] = b0;
+      rs[PINS_DDCG_MAX + rank] = b1;
+    }
+  }
   if (rank == 0 && tid == 0) {
     a.info[0] = (double)it;
     a.info[1] = (bb > 0.f) ? sqrt((double)rr / (double)bb) : 0.0;
   }
   cluster.sync();                                   // no CTA exits while others read its u
+  if (a.dots && rank == 0 && tid == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int q = 0; q < CS; ++q) { t0 += dslot[0][q]; t1 += dslot[1][q]; }
+    a.dots[0] = t0;
+    a.dots[1] = t1;
+  }
 }
 
 static int ddcg_cluster_size() {
@@ -449,9 +432,9 @@ size_t ddcg_smem_bytes(int N, int cs) {
 cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
-                          const double* rhs, double* x, int* ent_tgt, float2* ent_val,
-                          int* ent_row, float* ug, double rtol, int max_iter, double* info,
-                          int* flag, cudaStream_t st, bool* used) {
+                          const double* rhs, double* x, const double* ab, double* dots,
+                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, double rtol,
+                          int max_iter, double* info, int* flag, cudaStream_t st, bool* used) {
   *used = false;
   const int N = m + n;
   const int CS = ddcg_cluster_size();
@@ -462,7 +445,8 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
   a.m = m; a.n = n; a.inv_eta = 1.0 / eta;
   a.r = r; a.c = c; a.indptr = indptr; a.indices = indices; a.data = data;
   a.colptr = colptr; a.rowidx = rowidx; a.cdata = cdata;
-  a.rhs = rhs; a.x = x; a.ent_tgt = ent_tgt; a.ent_val = ent_val; a.ent_row = ent_row;
+  a.rhs = rhs; a.x = x; a.ab = ab; a.dots = dots;
+  a.ent_tgt = ent_tgt; a.ent_val = ent_val; a.ent_row = ent_row;
   a.ug = ug;
   a.smem_bytes = smem;
   a.rtol2 = (float)(rtol * rtol); a.max_iter = max_iter; a.info = info; a.flag = flag;

@@ -70,6 +70,58 @@ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   dd r; fast_two_sum(p, e, r.hi, r.lo); return r;
 }
 
+// FP64 -> double-float with integer operations only: hi = the sign, exponent and
+// top 23 stored significand bits (truncated), lo = the remaining 29 bits rounded
+// to FP32, so hi + lo carries ~48 significand bits.  The binary exponent is
+// lowered by `shift` (an exact scaling by 2^-shift).  Zero, FP64 subnormals and
+// scaled magnitudes below 2^-126 give 0; above 2^128 give inf; NaN stays NaN.
+__device__ __forceinline__ float2 split_f64(double v, int shift) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.f);
+  const int fe = e - 1023 + 127 - shift;
+  if (e == 0 || fe <= 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (fe >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
+  const unsigned rest = (unsigned)(mant & 0x1fffffffu);
+  // rest * 2^-52 is exact and normal; times 2^(fe - 127) may round if subnormal
+  float lo = __fmul_rn(__fmul_rn(__uint2float_rn(rest), 0x1p-52f), __uint_as_float((unsigned)fe << 23));
+  if (sign) lo = -lo;
+  return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ float2 ddv_mul(float2 a, float2 b) {
+  float p, e; two_prod(a.x, b.x, p, e);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float h, l; fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
+// y + f * v  (f FP32, v and y double-float), normalised
+__device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
+  float p, e; two_prod(f, v.x, p, e);
+  e = __fmaf_rn(f, v.y, e);
+  float s, t; two_sum(y.x, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(y.y, e));
+  float h, l; fast_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
+// acc += v * u (v double-float, u FP32), unnormalised accumulation
+__device__ __forceinline__ void ddv_acc_mul(float2& acc, float2 v, float u) {
+  float p, e; two_prod(v.x, u, p, e);
+  e = __fmaf_rn(v.y, u, e);
+  float s, t; two_sum(acc.x, p, s, t);
+  acc.x = s; acc.y = __fadd_rn(acc.y, __fadd_rn(t, e));
+}
+__device__ __forceinline__ float2 ddv_add(float2 a, float2 b) {
+  float s, t; two_sum(a.x, b.x, s, t);
+  t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+  float h, l; fast_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
+
 // exp of a double-float argument, double-float result with relative error
 // about 2^-45 (tested against FP64 exp).  Table-driven method of Tang (ACM TOMS
 // 15(2), 1989): z log2(e) = k/1024 + r, exp(z) = 2^(k >> 10) T[k & 1023] e^(r ln 2),
@@ -303,7 +355,8 @@ struct PassArgs {
   const double* F; const double* G;       // potentials
   const double* A64; const double* B64;   // FP64: A = F/eta - s, B = G/eta
   const float2* Add; const float2* Bdd;   // mixed: same as double-float pairs
-  const float2* A2dd; const float2* B2dd; // mixed Sinkhorn: log2(e) A, log2(e) B
+  float2 l2e_eta;                         // mixed Sinkhorn: log2(e) / eta as a pair
+  float2 s_l2e;                           // s log2(e) as a pair
   dd kappa2_dd;                           // log2(e) kappa_dd
   const double* a; const double* b;
   const float2* exp_table;                // 2^(q/1024) pairs (mixed)

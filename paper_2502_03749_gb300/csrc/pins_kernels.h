@@ -5,6 +5,10 @@
 
 namespace pins {
 
+// shared memory of one row segment (row LSE) or row block (column LSE) of the
+// streamed mixed Sinkhorn kernels
+#define PINS_ROW_SEG_SMEM_BYTES (96 * 1024)
+
 struct SparsifyState;
 struct TrialArgs;
 struct CertArgs;
@@ -91,23 +95,23 @@ cudaError_t launch_pcg_cluster(int m, int n, double eta, const double* r, const 
                                const double* rhs, double* x, double rtol, int max_iter,
                                double* info, int* flag, cudaStream_t st, bool* used);
 // Double-float CG of the mixed path (one cluster); *used = false when the
-// problem does not fit, and then nothing was launched.
+// problem does not fit, and then nothing was launched.  rhs == NULL: the
+// right-hand side is (ab - (r; c)); dots != NULL receives <rhs, x>, <ab, x>.
 cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
-                          const double* rhs, double* x, int* ent_tgt, float2* ent_val,
-                          int* ent_row, float* ug, double rtol, int max_iter, double* info,
-                          int* flag, cudaStream_t st, bool* used);
-void launch_prep2(const double* F, const double* G, int m, int n, double eta, double s,
-                  float2* A2dd, float2* B2dd, cudaStream_t st);
+                          const double* rhs, double* x, const double* ab, double* dots,
+                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, double rtol,
+                          int max_iter, double* info, int* flag, cudaStream_t st, bool* used);
 void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
 void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,
                        float2* Pdd, float2* Qdd, cudaStream_t st);
 void launch_grad(const double* a, const double* b, const double* r, const double* c, int m,
                  int n, double* g, cudaStream_t st);
-void launch_axpy2(double* F, double* G, const double* d, int m, int n, double alpha,
-                  cudaStream_t st);
+void launch_axpy_prep(double* F, double* G, const double* d, int m, int n, double alpha,
+                      double eta, double s, double* A64, double* B64, float2* Add, float2* Bdd,
+                      cudaStream_t st);
 void launch_outer(double* F, double* G, double* Phi, double* Psi, int m, int n, cudaStream_t st);
 void launch_dot2(const double* x1, const double* y1, const double* x2, const double* y2, int N,
                  double* out, cudaStream_t st);

@@ -18,7 +18,7 @@ int sm_count() {
   return v;
 }
 
-#define PINS_ROW_SEG_SMEM (96 * 1024)
+#define PINS_ROW_SEG_SMEM PINS_ROW_SEG_SMEM_BYTES
 
 template <int K> struct Launch {
   using P = PINS_POLICY<K>;
@@ -48,12 +48,24 @@ template <int K> struct Launch {
   static void col_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* G_out,
                       cudaStream_t st) {
     if constexpr (P::MIXED) {
-      // row blocks for ~4 CTAs per SM, at most g.gy (colpart0 holds g.gy * n)
-      const int gy = std::max(1, std::min({(4 * sm_count() + g.gx - 1) / g.gx, g.gy,
-                                           (p.m + PINS_WARPS - 1) / PINS_WARPS}));
+      // row blocks for ~4 CTAs per SM, at most g.gy (colpart0 holds g.gy * n), and
+      // enough of them for a block's A_i to fit in shared memory
+      const int rows_fit = PINS_ROW_SEG_SMEM / (int)sizeof(float2);
+      const int gy = std::max(1, std::min({std::max((4 * sm_count() + g.gx - 1) / g.gx,
+                                                    (p.m + rows_fit - 1) / rows_fit),
+                                           g.gy, (p.m + PINS_WARPS - 1) / PINS_WARPS}));
       const int rb = (p.m + gy - 1) / gy;
-      k_col_lse_mx<P><<<dim3(g.gx, gy), PINS_TPB, 0, st>>>(p, rb, ws, G_out);
-      return;
+      const size_t smem = sizeof(float2) * (size_t)rb;
+      if (smem <= PINS_ROW_SEG_SMEM) {
+        static bool configured = false;
+        if (!configured) {
+          cudaFuncSetAttribute(k_col_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               PINS_ROW_SEG_SMEM);
+          configured = true;
+        }
+        k_col_lse_mx<P><<<dim3(g.gx, gy), PINS_TPB, smem, st>>>(p, rb, ws, G_out);
+        return;
+      }
     }
     k_col_lse<P><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, G_out);
   }

@@ -1,8 +1,9 @@
 // Sinkhorn warm-up half-steps of the mixed policy (Algorithm 2 warm-up loop;
 // Algorithm 1 in log form), streamed with an online log-sum-exp in base 2.
 //
-// The passes read log2(e) A_i, log2(e) B_j and log2(e) kappa as double-float
-// pairs, so w = V - kappa C_ij is formed in double-float directly in log2 units
+// The passes form log2(e) A_i, log2(e) B_j (from the FP64 potentials, split by
+// integer operations) and log2(e) kappa as double-float pairs, so
+// w = V - kappa C_ij is formed in double-float directly in log2 units
 // and each entry costs one FP32 ex2 (flush-to-zero: a term below 2^-126 of the
 // running maximum is dropped).  Each thread keeps a running (M, S) with
 // S = sum 2^(w - M) and updates it four entries at a time: M' = max(M, the
@@ -53,6 +54,12 @@ __device__ __forceinline__ void lse2_merge(float& m1, float& s1, float m2, float
   m1 = mn;
 }
 
+// log2(e) A_i = (F_i / eta - s) log2(e) as a pair, from the FP64 F_i
+__device__ __forceinline__ float2 a2_of(const PassArgs& p, int i) {
+  const float2 f = ddv_mul(split_f64(p.F[i], 0), p.l2e_eta);
+  return ddv_add(f, make_float2(-p.s_l2e.x, -p.s_l2e.y));
+}
+
 // 4 consecutive raw costs of row i from column j (entries at or beyond jend are
 // left unspecified); a 16-byte load when the dense row allows it
 template <class P>
@@ -82,7 +89,8 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
   const int x = blockIdx.x, y = blockIdx.y, SX = gridDim.x, GY = gridDim.y;
   const int j0 = x * seg, j1 = min(n, j0 + seg);
   const float kh = p.kappa2_dd.hi, kl = p.kappa2_dd.lo;
-  for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = p.B2dd[j];
+  // log2(e) B_j = G_j log2(e) / eta as a pair (integer split of the FP64 G_j)
+  for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = ddv_mul(split_f64(p.G[j], 0), p.l2e_eta);
   __syncthreads();
   for (int i = y * PINS_WARPS + warp; i < m; i += GY * PINS_WARPS) {
     float M = -INFINITY, S = 0.f;
@@ -138,7 +146,7 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
         lse2_merge(Mf, Sf, o.x, o.y);
       }
       const double lse2 = (double)Mf + log2((double)Sf);         // base-2 LSE_j of w
-      const double A2 = (double)p.A2dd[i].x + (double)p.A2dd[i].y;
+      const double A2 = (p.F[i] * p.inv_eta - p.s) * 1.4426950408889634074;
       const double ai = p.a[i];
       res += fabs(exp2(A2 + lse2) - ai);
       F_out[i] = p.eta * (log(ai) + p.s - LN2 * lse2);
@@ -158,11 +166,14 @@ template <class P>
 __global__ void __launch_bounds__(PINS_TPB)
 k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
   __shared__ float2 stg[PINS_WARPS][PINS_TC];
+  extern __shared__ float2 sA[];                 // log2(e) A_i of the row block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = p.m, n = p.n;
   const int i0 = blockIdx.y * rb, i1 = min(m, i0 + rb);
   const int nct = (n + PINS_TC - 1) / PINS_TC;
   const float kh = p.kappa2_dd.hi, kl = p.kappa2_dd.lo;
+  for (int i = i0 + threadIdx.x; i < i1; i += PINS_TPB) sA[i - i0] = a2_of(p, i);
+  __syncthreads();
   for (int ct = blockIdx.x; ct < nct; ct += gridDim.x) {
     const int jb = ct * PINS_TC + 4 * lane;
     const int nv = min(4, n - jb);                 // valid columns of this lane (may be <= 0)
@@ -177,7 +188,7 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
         float2 A[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          A[t] = p.A2dd[i + t * PINS_WARPS];
+          A[t] = sA[i + t * PINS_WARPS - i0];
           cost4<P>(p, i + t * PINS_WARPS, jb, n, c[t]);
         }
 #pragma unroll
@@ -190,7 +201,7 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
       }
       for (; i < i1; i += PINS_WARPS) {
         float c[4];
-        const float2 A = p.A2dd[i];
+        const float2 A = sA[i - i0];
         cost4<P>(p, i, jb, n, c);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -202,7 +213,7 @@ k_col_lse_mx(PassArgs p, int rb, MergeWS ws, double* G_out) {
     } else if (nv > 0) {
       for (int i = i0 + warp; i < i1; i += PINS_WARPS) {
         float c[4];
-        const float2 A = p.A2dd[i];
+        const float2 A = sA[i - i0];
         cost4<P>(p, i, jb, n, c);
         for (int q = 0; q < nv; ++q) {
           float wh, wl;

@@ -18,8 +18,9 @@
 namespace pins {
 
 struct TrialArgs {
-  const double* Pt64; const double* Qt64;     // FP64 path
-  const float2* Ptdd; const float2* Qtdd;     // mixed path
+  const double* Pt64; const double* Qt64;     // FP64 path: alpha df / eta, alpha dg / eta
+  const double* dir;                          // mixed path: (df; dg), m + n
+  float2 scale;                               // mixed path: alpha / eta as a pair
 };
 
 template <class P, bool TRIAL>
@@ -49,7 +50,8 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
       const int jc = jj[q] < n ? jj[q] : n - 1;
       cd[q] = P::col(p, jc);
       if constexpr (TRIAL) {
-        if constexpr (P::MIXED) Qf[q] = tr.Qtdd[jc]; else Qd[q] = tr.Qt64[jc];
+        if constexpr (P::MIXED) Qf[q] = ddv_mul(split_f64(tr.dir[m + jc], 0), tr.scale);
+        else Qd[q] = tr.Qt64[jc];
       }
     }
     double csum[PINS_CPL];
@@ -90,7 +92,7 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
           }
         } else {
           const float2 A = P::row(p, i);
-          const float2 Pt = TRIAL ? tr.Ptdd[i] : make_float2(0.f, 0.f);
+          const float2 Pt = TRIAL ? ddv_mul(split_f64(tr.dir[i], 0), tr.scale) : make_float2(0.f, 0.f);
           dd racc; racc.hi = 0.f; racc.lo = 0.f;
           float dfs = 0.f;
 #pragma unroll

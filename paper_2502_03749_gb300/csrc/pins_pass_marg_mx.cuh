@@ -29,7 +29,7 @@ namespace pins {
 // shared memory: exp table, B and Q of the segment, per-warp column sums
 // (PINS_WARPS x PINS_MSEG double-float), per-warp compaction lists
 #define PINS_MSEG_SMEM (sizeof(float2) * (PINS_EXP_TABLE + 2 * PINS_MSEG + PINS_WARPS * PINS_MSEG) + \
-                        (sizeof(float4) + sizeof(int)) * PINS_WARPS * PINS_MHALF)
+                        (sizeof(float2) + sizeof(int)) * PINS_WARPS * PINS_MHALF)
 
 template <class P, bool TRIAL>
 __global__ void __launch_bounds__(PINS_TPB)
@@ -39,7 +39,7 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
   float2* sB = s_tab + PINS_EXP_TABLE;
   float2* sQ = sB + PINS_MSEG;
   float2* cacc = sQ + PINS_MSEG;                            // [warp][column] sums
-  float4* lz = reinterpret_cast<float4*>(cacc + PINS_WARPS * PINS_MSEG);   // [warp][slot]
+  float2* lz = cacc + PINS_WARPS * PINS_MSEG;                // [warp][slot]
   int* lc = reinterpret_cast<int*>(lz + PINS_WARPS * PINS_MHALF);
   __shared__ double sh_red[PINS_WARPS];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -50,18 +50,18 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
   for (int q = threadIdx.x; q < PINS_EXP_TABLE; q += PINS_TPB) s_tab[q] = p.exp_table[q];
   for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) {
     sB[j - j0] = p.Bdd[j];
-    if constexpr (TRIAL) sQ[j - j0] = tr.Qtdd[j];
+    if constexpr (TRIAL) sQ[j - j0] = ddv_mul(split_f64(tr.dir[m + j], 0), tr.scale);
   }
   for (int q = threadIdx.x; q < PINS_WARPS * PINS_MSEG; q += PINS_TPB) cacc[q] = make_float2(0.f, 0.f);
   __syncthreads();
   float2* wacc = cacc + warp * PINS_MSEG;
-  float4* wlz = lz + warp * PINS_MHALF;
+  float2* wlz = lz + warp * PINS_MHALF;
   int* wlc = lc + warp * PINS_MHALF;
   const float kh = p.kappa_dd.hi, kl = p.kappa_dd.lo;
   float zmaxf = -INFINITY;
   for (int i = y * PINS_WARPS + warp; i < m; i += GY * PINS_WARPS) {
     const float2 A = p.Add[i];
-    const float2 Pt = TRIAL ? tr.Ptdd[i] : make_float2(0.f, 0.f);
+    const float2 Pt = TRIAL ? ddv_mul(split_f64(tr.dir[i], 0), tr.scale) : make_float2(0.f, 0.f);
     dd racc; racc.hi = 0.f; racc.lo = 0.f;
     float dfs = 0.f;
 #pragma unroll
@@ -80,31 +80,28 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
         for (int q = 0; q < 4; ++q) {
           const int j = jb + q;
           bool keep = false;
-          float zh = 0.f, zl = 0.f, z0 = 0.f, tf = 0.f;
+          float zh = 0.f, zl = 0.f;
           if (j < j1) {
             float wh, wl;
             dd_w(sB[j - j0], c[q], kh, kl, wh, wl);
             dd_z(A, wh, wl, zh, zl);
+            float zf = __fadd_rn(zh, zl);
             if constexpr (TRIAL) {
-              const float2 Q = sQ[j - j0];
-              float th, tl; two_sum(Pt.x, Q.x, th, tl);
-              tl = __fadd_rn(tl, __fadd_rn(Pt.y, Q.y));
-              z0 = __fadd_rn(zh, zl);
-              tf = __fadd_rn(th, tl);
-              float sh, se; two_sum(zh, th, sh, se);
-              se = __fadd_rn(se, __fadd_rn(zl, tl));
-              fast_two_sum(sh, se, zh, zl);
-              keep = (z0 > -87.0f) || (zh > -87.0f);
+              // FP32 estimate of the trial point's exponent: it only places the
+              // e^-87 skip threshold and the sparsify window; the listed
+              // entries get z + t in double-float below
+              const float z1 = __fadd_rn(zf, __fadd_rn(Pt.x, sQ[j - j0].x));
+              keep = (zf > -87.0f) || (z1 > -87.0f);
+              zf = z1;
             } else {
-              keep = zh > -87.0f;
+              keep = zf > -87.0f;
             }
-            // the FP32 value of z, as ranked by Sparsify
-            zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
+            zmaxf = fmaxf(zmaxf, zf);
           }
           const unsigned int bal = __ballot_sync(0xffffffffu, keep);
           if (keep) {
             const int pos = cnt + __popc(bal & lt);
-            wlz[pos] = make_float4(zh, zl, z0, tf);
+            wlz[pos] = make_float2(zh, zl);
             wlc[pos] = col0 + q;
           }
           cnt += __popc(bal);
@@ -113,9 +110,22 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
       __syncwarp();
       // 2. the listed entries, 32 at a time
       for (int l = lane; l < cnt; l += 32) {
-        const float4 zz = wlz[l];
+        const float2 zz = wlz[l];
         const int col = wlc[l];
-        const dd e = dd_exp(zz.x, zz.y, s_tab);
+        float zh = zz.x, zl = zz.y;
+        float z0 = 0.f, tf = 0.f;
+        if constexpr (TRIAL) {
+          // t = Pt_i + Qt_j and the trial point z + t in double-float
+          const float2 Q = sQ[col];
+          float th, tl; two_sum(Pt.x, Q.x, th, tl);
+          tl = __fadd_rn(tl, __fadd_rn(Pt.y, Q.y));
+          z0 = __fadd_rn(zh, zl);
+          tf = __fadd_rn(th, tl);
+          float sh, se; two_sum(zh, th, sh, se);
+          se = __fadd_rn(se, __fadd_rn(zl, tl));
+          fast_two_sum(sh, se, zh, zl);
+        }
+        const dd e = dd_exp(zh, zl, s_tab);
         dd_acc(racc, e.hi, e.lo);
         const float2 o = wacc[col];
         dd cc; cc.hi = o.x; cc.lo = o.y;
@@ -123,7 +133,7 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
         wacc[col] = make_float2(cc.hi, cc.lo);
         if constexpr (TRIAL) {
           // objective term X~ (expm1(t) - t) >= 0 in FP32 (no cancellation)
-          if (zz.z > -87.0f) dfs = __fmaf_rn(exp2f(zz.z * 1.4426950408889634f), expm1_minus_x(zz.w), dfs);
+          if (z0 > -87.0f) dfs = __fmaf_rn(exp2f(z0 * 1.4426950408889634f), expm1_minus_x(tf), dfs);
         }
       }
       __syncwarp();

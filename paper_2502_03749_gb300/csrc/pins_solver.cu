@@ -72,8 +72,6 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.ys = cv.take<double>(n); w.ec = cv.take<double>(n); w.c1 = cv.take<double>(n);
   w.v = cv.take<double>(n);
   w.Add = cv.take<float2>(m); w.Bdd = cv.take<float2>(n);
-  w.Ptdd = cv.take<float2>(m); w.Qtdd = cv.take<float2>(n);
-  w.A2dd = cv.take<float2>(m); w.B2dd = cv.take<float2>(n);
   w.mws.rowpart0 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart1 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart2 = cv.take<double>((size_t)g.gx * m);
@@ -397,8 +395,11 @@ PassArgs Solver::args(double s, const double* F, const double* G) {
   a.F = F; a.G = G;
   a.A64 = ws_.A64; a.B64 = ws_.B64;
   a.Add = ws_.Add; a.Bdd = ws_.Bdd;
-  a.A2dd = ws_.A2dd; a.B2dd = ws_.B2dd;
-  const double k2 = kd * 1.4426950408889634074;
+  const double L2E = 1.4426950408889634074;
+  const double le = L2E / eta_, sl = s * L2E;
+  a.l2e_eta = make_float2((float)le, (float)(le - (double)(float)le));
+  a.s_l2e = make_float2((float)sl, (float)(sl - (double)(float)sl));
+  const double k2 = kd * L2E;
   a.kappa2_dd.hi = (float)k2;
   a.kappa2_dd.lo = (float)(k2 - (double)a.kappa2_dd.hi);
   a.a = a_; a.b = b_;
@@ -417,14 +418,13 @@ void Solver::prep(double s) {
 }
 
 void Solver::sinkhorn_iter(double s, int t) {
-  // the mixed passes read the log2-scaled pairs only; Add/Bdd are refreshed
-  // by the next prep() before any other pass
+  // the streamed mixed passes form their potentials from F, G themselves; Add/Bdd
+  // are refreshed by the next prep() before any other pass.  Sizes whose row
+  // segment or row block does not fit in shared memory use the tiled kernels,
+  // which read Add/Bdd.
+  const bool tiled = n_ > 32 * (PINS_ROW_SEG_SMEM_BYTES / 8) || m_ > 64 * (PINS_ROW_SEG_SMEM_BYTES / 8);
   auto refresh = [&]() {
-    if (!mixed_) { prep(s); return; }
-    prof_begin(PC_VEC);
-    launch_prep2(ws_.F, ws_.G, m_, n_, eta_, s, ws_.A2dd, ws_.B2dd, stream_);
-    prof_end();
-    ++launches_;
+    if (!mixed_ || tiled) prep(s);
   };
   refresh();
   PassArgs pa = args(s, ws_.F, ws_.G);
@@ -438,11 +438,13 @@ void Solver::sinkhorn_iter(double s, int t) {
   launches_ += 2;
 }
 
-void Solver::marg(double s, bool trial) {
+void Solver::marg(double s, bool trial, double alpha) {
   PassArgs pa = args(s, ws_.F, ws_.G);
   prof_begin(trial ? PC_TRIAL : PC_MARG);
   if (trial) {
-    TrialArgs tr{ws_.Pt64, ws_.Qt64, ws_.Ptdd, ws_.Qtdd};
+    const double sc = alpha / eta_;
+    TrialArgs tr{ws_.Pt64, ws_.Qt64, ws_.dir,
+                 make_float2((float)sc, (float)(sc - (double)(float)sc))};
     ps_->marg(pa, geom_, ws_.mws, &tr, ws_.rt, ws_.ct, ws_.scal + SC_TRIAL, stream_);
   } else {
     ps_->marg(pa, geom_, ws_.mws, nullptr, ws_.r, ws_.c, ws_.scal + SC_MARG, stream_);
@@ -618,25 +620,22 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         tau_prev = (float)reinterpret_cast<const SparsifyState*>(h_scal_ + SC_STATE)->tau;
         fast_ok = fast_path;
       }
-      launch_grad(a_, b_, ws_.r, ws_.c, m, n, ws_.grad, stream_);
       cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // CG index-check flag
-      prof_begin(PC_CG);
+      // M d = grad with grad = (a - r; b - c); also <grad, d> and <ab, d> for the line search
       cudaError_t ce = run_cg(mixed_, m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
-                              ws_.sw.data, ws_.grad, ws_.dir, cfg.cg_rtol, max_cg,
-                              ws_.scal + SC_CG);
-      prof_end();
+                              ws_.sw.data, nullptr, ws_.dir, cfg.cg_rtol, max_cg,
+                              ws_.scal + SC_CG, ws_.ab, ws_.scal + SC_DOTS);
       if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
-      launch_dot2(ws_.grad, ws_.dir, ws_.ab, ws_.dir, m + n, ws_.scal + SC_DOTS, stream_);
-      launches_ += 3;
       bool accepted = false, redo = false;
       double alpha = 1.0;
       int q = 0;
       for (; q <= cfg.max_backtrack; ++q) {
-        launch_trial_prep(ws_.dir, m, n, alpha / eta_, mixed_ ? nullptr : ws_.Pt64,
-                          mixed_ ? nullptr : ws_.Qt64, mixed_ ? ws_.Ptdd : nullptr,
-                          mixed_ ? ws_.Qtdd : nullptr, stream_);
-        ++launches_;
-        marg(s, true);
+        if (!mixed_) {   // the mixed trial pass forms alpha d / eta itself
+          launch_trial_prep(ws_.dir, m, n, alpha / eta_, ws_.Pt64, ws_.Qt64, nullptr, nullptr,
+                            stream_);
+          ++launches_;
+        }
+        marg(s, true, alpha);
         // trial scalars, dot products, CG info, the CG index-check flag and the
         // one-pass selection state in one copy
         cudaMemcpyAsync(h_scal_ + SC_TRIAL, ws_.scal + SC_TRIAL,
@@ -681,9 +680,12 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       r.ls_trials += std::min(q + 1, cfg.max_backtrack + 1);
       ++steps;
       if (accepted) {
-        launch_axpy2(ws_.F, ws_.G, ws_.dir, m, n, alpha, stream_);
+        prof_begin(PC_VEC);
+        launch_axpy_prep(ws_.F, ws_.G, ws_.dir, m, n, alpha, eta_, s, mixed_ ? nullptr : ws_.A64,
+                         mixed_ ? nullptr : ws_.B64, mixed_ ? ws_.Add : nullptr,
+                         mixed_ ? ws_.Bdd : nullptr, stream_);
+        prof_end();
         ++launches_;
-        prep(s);
         std::swap(ws_.r, ws_.rt);
         std::swap(ws_.c, ws_.ct);
         res = h_scal_[SC_TRIAL + 0];
@@ -802,19 +804,34 @@ pins_status Solver::step_sparsify(const pins_config& cfg, const pins_problem& p,
 cudaError_t Solver::run_cg(bool mixed, int m, int n, double eta, const double* r,
                            const double* c, const int* indptr, const int* indices,
                            const double* data, const double* rhs, double* d, double rtol,
-                           int max_iter, double* info) {
+                           int max_iter, double* info, const double* ab, double* dots) {
+  prof_begin(PC_CG);
   if (mixed) {
+    // the double-float kernel forms rhs = ab - (r; c) itself when rhs is NULL and
+    // writes the two inner products of the line search
     bool used = false;
     cudaError_t ce = launch_pcg_dd(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
-                                   ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.ent_tgt, ws_.ent_val,
-                                   ws_.ent_row, ws_.cg_u,
-                                   rtol, max_iter, info,
+                                   ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ab, dots, ws_.ent_tgt,
+                                   ws_.ent_val, ws_.ent_row, ws_.cg_u, rtol, max_iter, info,
                                    reinterpret_cast<int*>(ws_.scal + SC_FLAG), stream_, &used);
-    if (used) return ce;
+    if (used) { prof_end(); ++launches_; return ce; }
   }
-  return launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr, ws_.sw.rowidx,
-                    ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p, ws_.cg_q, ws_.cg_part, rtol,
-                    max_iter, info, reinterpret_cast<int*>(ws_.scal + SC_FLAG), sms_, stream_);
+  if (!rhs) {
+    launch_grad(a_, b_, r, c, m, n, ws_.grad, stream_);
+    rhs = ws_.grad;
+    ++launches_;
+  }
+  cudaError_t ce = launch_pcg(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
+                              ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ws_.cg_res, ws_.cg_p, ws_.cg_q,
+                              ws_.cg_part, rtol, max_iter, info,
+                              reinterpret_cast<int*>(ws_.scal + SC_FLAG), sms_, stream_);
+  prof_end();
+  ++launches_;
+  if (dots) {
+    launch_dot2(rhs, d, ab, d, m + n, dots, stream_);
+    ++launches_;
+  }
+  return ce;
 }
 
 pins_status Solver::step_cg(int m, int n, double eta, const double* r, const double* c,
@@ -828,7 +845,7 @@ pins_status Solver::step_cg(int m, int n, double eta, const double* r, const dou
   build_csc_from_csr(indptr, indices, data, m, n, nnz, ws_.sw, stream_);
   cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // index-check flag
   cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, rhs, d, rtol,
-                          max_iter, info);
+                          max_iter, info, nullptr, nullptr);
   launches_ += 5;
   if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); return PINS_ERR_CUDA; }
   return sync("step_cg");
@@ -858,10 +875,10 @@ pins_status Solver::step_objective_increase(const pins_config& cfg, const pins_p
     launch_dot2(ws_.ab, ws_.dir, nullptr, nullptr, m_ + n_, ws_.scal + SC_DOTS, stream_);
     ++launches_;
   }
-  launch_trial_prep(ws_.dir, m_, n_, alpha / eta_, mixed_ ? nullptr : ws_.Pt64,
-                    mixed_ ? nullptr : ws_.Qt64, mixed_ ? ws_.Ptdd : nullptr,
-                    mixed_ ? ws_.Qtdd : nullptr, stream_);
-  marg(s, true);
+  if (!mixed_)
+    launch_trial_prep(ws_.dir, m_, n_, alpha / eta_, ws_.Pt64, ws_.Qt64, nullptr, nullptr,
+                      stream_);
+  marg(s, true, alpha);
   ++launches_;
   cudaMemcpyAsync(h_scal_, ws_.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   if ((st = sync("step_objective_increase")) != PINS_OK) return st;

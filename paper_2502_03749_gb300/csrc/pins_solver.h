@@ -18,7 +18,7 @@ struct Workspace {
   double *F, *G, *Phi, *Psi, *A64, *B64, *r, *c, *rt, *ct, *Pt64, *Qt64;
   double *grad, *dir, *cg_res, *cg_p, *cg_q, *ab;
   double *xs, *u, *rr, *cr, *cp, *tc, *u2, *ys, *ec, *c1, *v;
-  float2 *Add, *Bdd, *Ptdd, *Qtdd, *A2dd, *B2dd;
+  float2 *Add, *Bdd;
   MergeWS mws;
   SparsifyState* st;
   unsigned int* hist;
@@ -78,10 +78,12 @@ class Solver {
 
   const std::string& error() const { return err_; }
   // the CG of one Newton step (double-float cluster kernel on the mixed path when
-  // it fits, else the FP64 kernels)
+  // it fits, else the FP64 kernels).  rhs == NULL: rhs = (a - r; b - c).  dots
+  // (may be NULL) receives <rhs, d> and <ab, d>.
   cudaError_t run_cg(bool mixed, int m, int n, double eta, const double* r, const double* c,
                      const int* indptr, const int* indices, const double* data,
-                     const double* rhs, double* d, double rtol, int max_iter, double* info);
+                     const double* rhs, double* d, double rtol, int max_iter, double* info,
+                     const double* ab, double* dots);
   long long launches() const { return launches_; }
 
   // Optional per-kernel-class device timing: CUDA events recorded on the
@@ -110,7 +112,7 @@ class Solver {
   pins_status sync(const char* where);
   void prep(double s);
   void sinkhorn_iter(double s, int t);
-  void marg(double s, bool trial);
+  void marg(double s, bool trial, double alpha = 0.0);
   pins_status sparsify(double s, int keep, double zmax, int* nnz_out);
   // one-pass selection for the later Newton steps of an outer iteration (mixed);
   // launches only, the outcome is read at the next line-search sync

@@ -414,23 +414,6 @@ void launch_prep(const double* F, const double* G, int m, int n, double eta, dou
   k_prep<<<blocks, 256, 0, st>>>(F, G, m, n, 1.0 / eta, s, A64, B64, Add, Bdd);
 }
 
-// log2(e) A_i and log2(e) B_j as double-float pairs (mixed Sinkhorn passes)
-__global__ void k_prep2(const double* F, const double* G, int m, int n, double inv_eta,
-                        double s, float2* A2dd, float2* B2dd) {
-  const double L2E = 1.4426950408889634074;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += gridDim.x * blockDim.x) {
-    const double v = ((t < m) ? F[t] * inv_eta - s : G[t - m] * inv_eta) * L2E;
-    const float hi = __double2float_rn(v);
-    const float lo = __double2float_rn(v - (double)hi);
-    if (t < m) A2dd[t] = make_float2(hi, lo); else B2dd[t - m] = make_float2(hi, lo);
-  }
-}
-void launch_prep2(const double* F, const double* G, int m, int n, double eta, double s,
-                  float2* A2dd, float2* B2dd, cudaStream_t st) {
-  int N = m + n; int blocks = (N + 255) / 256; if (blocks > 512) blocks = 512;
-  k_prep2<<<blocks, 256, 0, st>>>(F, G, m, n, 1.0 / eta, s, A2dd, B2dd);
-}
-
 // trial increments Pt_i = alpha df_i / eta, Qt_j = alpha dg_j / eta
 __global__ void k_trial_prep(const double* d, int m, int n, double scale, double* P64,
                              double* Q64, float2* Pdd, float2* Qdd) {
@@ -461,15 +444,25 @@ void launch_grad(const double* a, const double* b, const double* r, const double
 }
 
 // (F, G) += alpha d
-__global__ void k_axpy2(double* F, double* G, const double* d, int m, int n, double alpha) {
+// (F; G) += alpha d, then A = F/eta - s, B = G/eta (as k_prep) in the same launch
+__global__ void k_axpy_prep(double* F, double* G, const double* d, int m, int n, double alpha,
+                            double inv_eta, double s, double* A64, double* B64, float2* Add,
+                            float2* Bdd) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += gridDim.x * blockDim.x) {
-    if (t < m) F[t] += alpha * d[t]; else G[t - m] += alpha * d[t];
+    double v;
+    if (t < m) { v = F[t] + alpha * d[t]; F[t] = v; v = v * inv_eta - s; }
+    else { v = G[t - m] + alpha * d[t]; G[t - m] = v; v = v * inv_eta; }
+    float hi = __double2float_rn(v);
+    float lo = __double2float_rn(v - (double)hi);
+    if (t < m) { if (A64) A64[t] = v; if (Add) Add[t] = make_float2(hi, lo); }
+    else { if (B64) B64[t - m] = v; if (Bdd) Bdd[t - m] = make_float2(hi, lo); }
   }
 }
-void launch_axpy2(double* F, double* G, const double* d, int m, int n, double alpha,
-                  cudaStream_t st) {
+void launch_axpy_prep(double* F, double* G, const double* d, int m, int n, double alpha,
+                      double eta, double s, double* A64, double* B64, float2* Add, float2* Bdd,
+                      cudaStream_t st) {
   int N = m + n; int blocks = (N + 255) / 256; if (blocks > 512) blocks = 512;
-  k_axpy2<<<blocks, 256, 0, st>>>(F, G, d, m, n, alpha);
+  k_axpy_prep<<<blocks, 256, 0, st>>>(F, G, d, m, n, alpha, 1.0 / eta, s, A64, B64, Add, Bdd);
 }
 
 // outer update (reading R2): f = F - Phi; Phi = F; F = F + f (same for G)
