@@ -4,25 +4,27 @@
 //
 // Why double-float: this GPU issues FP64 at ~1/70 of its FP32 rate, and a CG
 // iteration on a few thousand unknowns is a chain of short dependent steps, so
-// FP64 latency sets its length.  The recurrences that carry the solution keep
-// ~48 significand bits:
-//   x, r, p, s (double-float), w = M u (double-float SpMV, diagonal and S
-//   entries scaled by 1/eta in double-float),
-// while two things that only steer the iteration run in FP32:
-//   u = D^-1 r rounded to FP32 (a fixed diagonal preconditioner applied with
-//   relative error 2^-24; w is computed exactly from this u, so s = M p and
-//   r = rhs - M x hold to double-float accuracy), and the three inner products
-//   (r.u, w.u, r.r), whose FP32 rounding perturbs the step lengths alpha, beta
-//   by ~1e-6 relatively and so changes the rate, not the fixed point.
-// rhs is scaled by a power of two (exact) so that its largest entry is in
-// [1, 2); x is scaled back at the end.
+// FP64 latency sets its length.  Every vector and the matrix-vector product
+// (diagonal and S entries scaled by 1/eta) keep ~48 significand bits; only the
+// three inner products per iteration (r.u, w.u, r.r) are FP32 sums, which
+// perturb the step lengths alpha, beta by ~1e-6 relatively and so change the
+// rate, not the fixed point.  The preconditioner is D^-1 with D^-1 rounded to
+// FP32 (a fixed diagonal).  rhs is scaled by a power of two (exact) so that its
+// largest entry is in [1, 2); x is scaled back at the end.
 //
-// Ordering: the single-reduction PCG of Chronopoulos & Gear (J. Comput. Appl.
-// Math. 25, 1989), as in the FP64 cluster kernel: per iteration
-//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
-//   [cluster barrier]  w = M u,  (r.u, w.u, r.r)  [cluster barrier]
-//   beta = g'/g, alpha = g'/(d' - beta g'/alpha).
-// Every CTA sums the 16 block partials in the same order and takes the same
+// Ordering: the pipelined PCG of Ghysels & Vanroose (Parallel Computing 40,
+// 2014), which puts the one global reduction of an iteration and its
+// matrix-vector product behind the same synchronisation:
+//   (r.u, w.u, r.r) partials, m = D^-1 w        -> publish    [cluster barrier]
+//   gamma, delta, rr (every CTA, same order);  stop if rr <= rtol^2 rr_0
+//   beta = gamma/gamma', alpha = gamma/(delta - beta gamma/alpha');  n = M m
+//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
+//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.
+// In exact arithmetic these are the iterates, and the iteration count, of the
+// textbook Jacobi PCG with the same stopping rule.  The m slices go through L2
+// (two alternating buffers, so one barrier per iteration suffices), the block
+// partials through distributed shared memory (two alternating slot sets).
+// Every CTA sums the block partials in the same order and takes the same
 // decisions, so results are reproducible run to run.
 #include <cooperative_groups.h>
 #include "pins_kernels.h"
@@ -35,8 +37,8 @@ namespace pins {
 #define PINS_DDCG_MAX 16
 #define PINS_DDCG_TPB 256
 #define PINS_DDCG_SMEM (200 * 1024)
-// shared bytes per unknown: r, x, p, s, w, diag, od (7 x 8) + u (4) + D^-1 (4) + row begin (4)
-#define PINS_DDCG_PER_UNKNOWN 68
+// shared bytes per unknown: x, r, u, w, z, q, s, p, m, diag, od (11 x 8) + D^-1 (4) + row begin (4)
+#define PINS_DDCG_PER_UNKNOWN 96
 
 struct CGddArgs {
   int m, n;
@@ -58,7 +60,7 @@ struct CGddArgs {
 __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
-  __shared__ float slot[3 * PINS_DDCG_MAX];
+  __shared__ float slot[2][3][PINS_DDCG_MAX];     // double-buffered block partials
   __shared__ unsigned int eslot[1];
   __shared__ double dred[2][PINS_DDCG_TPB / 32];
   __shared__ double dslot[2][PINS_DDCG_MAX];
@@ -73,21 +75,25 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   const int L = (N + CS - 1) / CS;
   const int lo = rank * L;
   const int nl = max(0, min(N, lo + L) - lo);
-  // shared memory: the own slice (7 double-float and 2 FP32 arrays of L4, L4 + 4
-  // row offsets), then, when the dynamic allocation has room, this CTA's packed
-  // entries (target, value / eta, local row)
+  // shared memory: the own slice (11 double-float arrays and 1 FP32 array of L4,
+  // L4 + 4 row offsets), then, when the dynamic allocation has room, this CTA's
+  // packed entries (target, value / eta, local row)
   const int L4 = (L + 3) & ~3;
-  float2* rv = reinterpret_cast<float2*>(ddcg_smem);
-  float2* xv = rv + L4;
-  float2* pv = xv + L4;
-  float2* sv = pv + L4;
-  float2* wv = sv + L4;
-  float2* dg = wv + L4;       // diag / eta
-  float2* od = dg + L4;       // off-diagonal part of M u (zeroed after use)
-  float* u = reinterpret_cast<float*>(od + L4);  // own slice (also published in a.ug)
-  float* dinv = u + L4;
+  float2* xv = reinterpret_cast<float2*>(ddcg_smem);
+  float2* rv = xv + L4;
+  float2* uv = rv + L4;       // D^-1 r (recurrence)
+  float2* wv = uv + L4;       // M u
+  float2* zv = wv + L4;
+  float2* qv = zv + L4;
+  float2* sv = qv + L4;
+  float2* pv = sv + L4;
+  float2* mv = pv + L4;       // D^-1 w (published in the exchange buffer)
+  float2* dg = mv + L4;       // diag / eta
+  float2* od = dg + L4;       // off-diagonal part of M m (zeroed after use)
+  float* dinv = reinterpret_cast<float*>(od + L4);
   int* rb = reinterpret_cast<int*>(dinv + L4);   // nl + 1 entry offsets (relative to E0)
   const size_t base_bytes = sizeof(float) * (size_t)(PINS_DDCG_PER_UNKNOWN / 4) * L4 + 16;
+  float2* mg = reinterpret_cast<float2*>(a.ug);  // two buffers of N pairs
 
   const int Kc = __ldg(a.indptr + m);
   auto beg = [&](int t) -> int {
@@ -134,8 +140,10 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     dg[k] = dd_;
     dinv[k] = __frcp_rn(dd_.x);
     xv[k] = make_float2(0.f, 0.f);
-    pv[k] = make_float2(0.f, 0.f);
+    zv[k] = make_float2(0.f, 0.f);
+    qv[k] = make_float2(0.f, 0.f);
     sv[k] = make_float2(0.f, 0.f);
+    pv[k] = make_float2(0.f, 0.f);
     od[k] = make_float2(0.f, 0.f);
     const int b0 = beg(t) - E0, b1 = beg(t + 1) - E0;
     rb[k] = b0;
@@ -160,12 +168,14 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   unsigned int E = 0u;
   for (int q = 0; q < CS; ++q) E = max(E, *cluster.map_shared_rank(eslot, q));
   const int shift = (int)E - 1023;                  // max |rhs| 2^-shift in [1, 2)
-  float lr = 0.f;
+  // r0 = rhs (scaled), u0 = D^-1 r0, published in exchange buffer 1 for w0 = M u0
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
     const float2 r0 = split_f64(rhs_of(lo + k), shift);
     rv[k] = r0;
-    u[k] = __fmul_rn(dinv[k], r0.x);
-    __stcg(a.ug + lo + k, u[k]);
+    const float2 u0 = ddv_scale(dinv[k], r0);
+    uv[k] = u0;
+    mv[k] = u0;
+    __stcg(mg + N + lo + k, u0);
   }
   // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
   const int ne = E1 - E0;
@@ -187,7 +197,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // Products first (independent), then a sum over runs of equal local row; a
   // row cut by the slice start is this thread's head, a row cut by its end its
   // tail (completed below from the following threads' heads, in thread order).
-  auto spmv = [&]() {
+  auto spmv = [&](const float2* src) {
     float2 headv = make_float2(0.f, 0.f), tailv = make_float2(0.f, 0.f);
     int headrow = -1, tailrow = -1;
     if (c0 < c1) {
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
       bool first = true;
       float2 acc = make_float2(0.f, 0.f);
       for (int base = c0; base < c1; base += 4) {
-        int tg[4], rw[4]; float2 v[4]; float uu[4], ph[4], pl[4];
+        int tg[4], rw[4]; float2 v[4], uu[4]; float ph[4], pl[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const bool ok = base + q < c1;
@@ -204,11 +214,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
           rw[q] = ok ? erow[base + q] : cur;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) uu[q] = __ldcg(a.ug + tg[q]);
+        for (int q = 0; q < 4; ++q) uu[q] = __ldcg(src + tg[q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          two_prod(v[q].x, uu[q], ph[q], pl[q]);
-          pl[q] = __fmaf_rn(v[q].y, uu[q], pl[q]);
+          two_prod(v[q].x, uu[q].x, ph[q], pl[q]);
+          pl[q] = __fmaf_rn(v[q].x, uu[q].y, __fmaf_rn(v[q].y, uu[q].x, pl[q]));
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -243,9 +253,9 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     }
     __syncthreads();
   };
-  // three block partials -> every CTA's slots -> cluster barrier -> every warp
-  // sums the slots in the same butterfly order (bit-identical in all lanes/CTAs)
-  auto reduce3 = [&](float v0, float v1, float v2, float& t0r, float& t1r, float& t2r) {
+  // three block partials -> slot buffer `b` of every CTA (the cluster barrier
+  // that follows publishes them)
+  auto publish3 = [&](float v0, float v1, float v2, int b) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v0 += __shfl_xor_sync(0xffffffffu, v0, o);
@@ -266,16 +276,19 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
         b2 += __shfl_xor_sync(0xffffffffu, b2, o);
       }
       if (lane < CS) {
-        float* rs = cluster.map_shared_rank(slot, lane);
+        float* rs = cluster.map_shared_rank(&slot[b][0][0], lane);
         rs[0 * PINS_DDCG_MAX + rank] = b0;
         rs[1 * PINS_DDCG_MAX + rank] = b1;
         rs[2 * PINS_DDCG_MAX + rank] = b2;
       }
     }
-    cluster.sync();
-    float q0 = lane < CS ? slot[0 * PINS_DDCG_MAX + lane] : 0.f;
-    float q1 = lane < CS ? slot[1 * PINS_DDCG_MAX + lane] : 0.f;
-    float q2 = lane < CS ? slot[2 * PINS_DDCG_MAX + lane] : 0.f;
+  };
+  // every warp sums the slots of buffer `b` in the same butterfly order
+  // (bit-identical in all lanes and CTAs)
+  auto gather3 = [&](int b, float& t0r, float& t1r, float& t2r) {
+    float q0 = lane < CS ? slot[b][0][lane] : 0.f;
+    float q1 = lane < CS ? slot[b][1][lane] : 0.f;
+    float q2 = lane < CS ? slot[b][2][lane] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       q0 += __shfl_xor_sync(0xffffffffu, q0, o);
@@ -284,86 +297,76 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     }
     t0r = q0; t1r = q1; t2r = q2;
   };
-  // w = diag u + od, od reset; partial inner products
-  auto apply_w = [&](float& lg, float& ld, float& lrr) {
-    lg = 0.f; ld = 0.f; lrr = 0.f;
-    for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
-      const int k2 = k + PINS_DDCG_TPB;
-      const bool two = k2 < nl;
-      const int kk[2] = {k, two ? k2 : k};
-      float uk[2], rk[2]; float2 w[2], dgk[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uk[h] = u[kk[h]]; w[h] = od[kk[h]]; dgk[h] = dg[kk[h]]; rk[h] = rv[kk[h]].x;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        ddv_acc_mul(w[h], dgk[h], uk[h]);
-        float hh, ll; fast_two_sum(w[h].x, w[h].y, hh, ll);
-        w[h] = make_float2(hh, ll);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !two) break;
-        wv[kk[h]] = w[h];
-        od[kk[h]] = make_float2(0.f, 0.f);
-        lg = __fmaf_rn(rk[h], uk[h], lg);
-        ld = __fmaf_rn(w[h].x, uk[h], ld);
-        lrr = __fmaf_rn(rk[h], rk[h], lrr);
-      }
-    }
-  };
 
-  cluster.sync();                                   // every u slice ready
-  spmv();
-  float lg, ld;
-  apply_w(lg, ld, lr);
-  float gam, dlt, bb;
-  reduce3(lg, ld, lr, gam, dlt, bb);
-  float alpha = (dlt != 0.f) ? gam / dlt : 0.f;
-  float beta = 0.f;
-  float rr = bb;
-  int it = 0;
-  bool stop = !(bb > 0.f);
-  while (!stop && it < a.max_iter) {
+  // w0 = M u0
+  cluster.sync();                                   // every u0 slice published
+  spmv(mg + N);
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    wv[k] = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
+    od[k] = make_float2(0.f, 0.f);
+  }
+  int it = 0, buf = 0;
+  float gam_prev = 1.f, alpha_prev = 1.f, bb = 0.f, rr = 0.f;
+  while (true) {
+    // phase A (own unknowns): (r.u, w.u, r.r) partials; m = D^-1 w published
+    float lg = 0.f, ld = 0.f, lrr = 0.f;
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float2 w = wv[k];
+      const float rk = rv[k].x, uk = uv[k].x;
+      lg = __fmaf_rn(rk, uk, lg);
+      ld = __fmaf_rn(w.x, uk, ld);
+      lrr = __fmaf_rn(rk, rk, lrr);
+      const float2 mk = ddv_scale(dinv[k], w);
+      mv[k] = mk;
+      __stcg(mg + (size_t)buf * N + lo + k, mk);
+    }
+    publish3(lg, ld, lrr, buf);
+    cluster.sync();                                 // m slices and partials published
+    // phase B: scalars (identical in every CTA), then n = M m
+    float gam, dlt;
+    gather3(buf, gam, dlt, rr);
+    if (it == 0) bb = rr;
+    if (!(bb > 0.f) || !(rr > a.rtol2 * bb) || it >= a.max_iter) break;   // NaN stops
+    const float beta = (it == 0) ? 0.f : gam / gam_prev;
+    const float alpha = (it == 0) ? gam / dlt : gam / (dlt - beta * gam / alpha_prev);
+    spmv(mg + (size_t)buf * N);
     // two unknowns per step, loads first, so their dependency chains overlap
     for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
       const int k2 = k + PINS_DDCG_TPB;
       const bool two = k2 < nl;
       const int kk[2] = {k, two ? k2 : k};
-      float uk[2], di[2]; float2 p0[2], s0[2], w0[2], x0[2], r0[2];
+      float2 n0[2], z0[2], q0[2], s0[2], p0[2], x0[2], r0[2], u0[2], w0[2], m0[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        uk[h] = u[kk[h]]; di[h] = dinv[kk[h]]; p0[h] = pv[kk[h]]; s0[h] = sv[kk[h]];
-        w0[h] = wv[kk[h]]; x0[h] = xv[kk[h]]; r0[h] = rv[kk[h]];
+        const int t = kk[h];
+        n0[h] = ddv_add(ddv_mul(dg[t], mv[t]), od[t]);
+        z0[h] = zv[t]; q0[h] = qv[t]; s0[h] = sv[t]; p0[h] = pv[t];
+        x0[h] = xv[t]; r0[h] = rv[t]; u0[h] = uv[t]; w0[h] = wv[t]; m0[h] = mv[t];
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        p0[h] = ddv_axpy(beta, p0[h], make_float2(uk[h], 0.f));
+        z0[h] = ddv_axpy(beta, z0[h], n0[h]);
+        q0[h] = ddv_axpy(beta, q0[h], m0[h]);
         s0[h] = ddv_axpy(beta, s0[h], w0[h]);
+        p0[h] = ddv_axpy(beta, p0[h], u0[h]);
         x0[h] = ddv_axpy(alpha, p0[h], x0[h]);
         r0[h] = ddv_axpy(-alpha, s0[h], r0[h]);
-        uk[h] = __fmul_rn(di[h], r0[h].x);
+        u0[h] = ddv_axpy(-alpha, q0[h], u0[h]);
+        w0[h] = ddv_axpy(-alpha, z0[h], w0[h]);
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (h == 1 && !two) break;
-        pv[kk[h]] = p0[h]; sv[kk[h]] = s0[h]; xv[kk[h]] = x0[h]; rv[kk[h]] = r0[h];
-        u[kk[h]] = uk[h];
-        __stcg(a.ug + lo + kk[h], uk[h]);
+        const int t = kk[h];
+        od[t] = make_float2(0.f, 0.f);
+        zv[t] = z0[h]; qv[t] = q0[h]; sv[t] = s0[h]; pv[t] = p0[h];
+        xv[t] = x0[h]; rv[t] = r0[h]; uv[t] = u0[h]; wv[t] = w0[h];
       }
     }
+    gam_prev = gam;
+    alpha_prev = alpha;
     ++it;
-    cluster.sync();                                 // every u slice updated
-    spmv();
-    apply_w(lg, ld, lr);
-    float gn, dn;
-    reduce3(lg, ld, lr, gn, dn, rr);
-    stop = !(rr > a.rtol2 * bb);                    // ||r|| <= rtol ||rhs|| (NaN stops)
-    if (stop) break;
-    beta = gn / gam;
-    alpha = gn / (dn - beta * gn / alpha);
-    gam = gn;
+    buf ^= 1;
   }
   const double scale = ldexp(1.0, shift);
   double dg0 = 0.0, dg1 = 0.0;                      // <rhs, x>, <ab, x> partials

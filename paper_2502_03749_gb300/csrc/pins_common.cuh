@@ -99,6 +99,13 @@ __device__ __forceinline__ float2 ddv_mul(float2 a, float2 b) {
   float h, l; fast_two_sum(p, e, h, l);
   return make_float2(h, l);
 }
+// f * v (f FP32, v double-float), normalised
+__device__ __forceinline__ float2 ddv_scale(float f, float2 v) {
+  float p, e; two_prod(f, v.x, p, e);
+  e = __fmaf_rn(f, v.y, e);
+  float h, l; fast_two_sum(p, e, h, l);
+  return make_float2(h, l);
+}
 // y + f * v  (f FP32, v and y double-float), normalised
 __device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
   float p, e; two_prod(f, v.x, p, e);

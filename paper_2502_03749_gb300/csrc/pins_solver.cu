@@ -97,7 +97,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.fkey = cv.take<float>(PINS_FAST_CAP); w.fij = cv.take<unsigned long long>(PINS_FAST_CAP);
   w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
   w.ent_row = cv.take<int>(2 * (size_t)kcap);
-  w.cg_u = cv.take<float>((size_t)N);
+  w.cg_u = cv.take<float>(4 * (size_t)N);   // two buffers of N double-float pairs
   w.cg_part = cv.take<double>(3 * 64 + 8);
   w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
   w.a = ip.ab ? cv.take<double>(m) : nullptr;
