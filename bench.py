@@ -41,6 +41,17 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="plain FP64 solves timed for the comparison key (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving", action="store_true",
+                    help="instead of the contract line: a served request stream (Poisson "
+                         "arrivals of point-cloud pairs) with p50/p99 latency, mixed served vs "
+                         "plain FP64 one at a time")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=100.0, help="arrivals per second")
+    ap.add_argument("--serve-nmin", type=int, default=256)
+    ap.add_argument("--serve-nmax", type=int, default=2048)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-fp64", type=int, default=-1,
+                    help="requests of the stream solved by the FP64 arm (-1: all)")
     return ap.parse_args()
 
 
@@ -393,8 +404,83 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- #
+# serving stream (separate mode, not the contract line)
+# --------------------------------------------------------------------------- #
+def run_serving(args):
+    """Requests of point-cloud pairs (n log-uniform in [nmin, nmax], GMM points,
+    Dirichlet(1) weights, certified-gap target 1e-6, paper-default caps) arrive as
+    a Poisson stream.  Mixed arm: pins_submit at each arrival time on one handle
+    (max_inflight concurrent solves, device-memory admission), completions found
+    with pins_poll.  FP64 arm: the same requests solved one at a time in arrival
+    order (FIFO).  Latency = completion - arrival."""
+    import torch
+    from paper_2502_03749_gb300 import pins, workloads as wl
+    R = args.serve_requests
+    reqs = [wl.serving_request(i, eta=args.eta, n_min=args.serve_nmin, n_max=args.serve_nmax)
+            for i in range(R)]
+    refs = [pins.problem_from_workload(w) for w in reqs]
+    arr = wl.poisson_arrivals(args.serve_rate, R)
+    arr = arr - arr[0]
+    common = dict(eta=args.eta, K=args.K, tol_gap=1e-6, gap_every=10)
+    # warm-up (module load, first-touch allocations)
+    hw = pins.Pins(prec="mixed", **common)
+    hw.solve(pins.problem_from_workload(wl.serving_request(10**6, eta=args.eta, n_min=256, n_max=256)))
+    hw.close()
+    h = pins.Pins(prec="mixed", max_inflight=args.serve_inflight, **common)
+    done = {}
+    pending = {}
+    t0 = time.perf_counter()
+    k = 0
+    while len(done) < R:
+        now = time.perf_counter() - t0
+        while k < R and arr[k] <= now:
+            pending[h.submit(refs[k])] = k
+            k += 1
+        for t in list(pending):
+            d = h.poll(t)
+            if d is not None:
+                done[pending.pop(t)] = (time.perf_counter() - t0, d)
+        time.sleep(0.0005)
+    h.close()
+    lat = np.array([done[i][0] - arr[i] for i in range(R)])
+    span = max(v[0] for v in done.values())
+    gaps = [done[i][1]["rel_gap"] for i in range(R)]
+    nf = R if args.serve_fp64 < 0 else min(R, args.serve_fp64)
+    h64 = pins.Pins(prec="fp64", **common)
+    finish, t_prev, solve_s = [], 0.0, []
+    for i in range(nf):
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        h64.solve(refs[i], want_potentials=False)
+        dt = time.perf_counter() - ts
+        solve_s.append(dt)
+        t_prev = max(t_prev, arr[i]) + dt
+        finish.append(t_prev)
+    h64.close()
+    lat64 = np.array([finish[i] - arr[i] for i in range(nf)])
+    ns = [r.prob.n for r in refs]
+    line = {"mode": "serving", "metric": "OT solves/s + p50/p99 latency", "unit": "solves/s",
+            "requests": R, "rate_per_s": args.serve_rate,
+            "n_range": [args.serve_nmin, args.serve_nmax], "n_median": float(np.median(ns)),
+            "config": {"eta": args.eta, "K": args.K, "T1": 100, "T2": 50, "tol_gap": 1e-6,
+                       "points": "8-component 2-D GMM, Dirichlet(1) weights, cost /max",
+                       "max_inflight": args.serve_inflight},
+            "mixed_served": {"solves_per_s": R / span, "p50_s": float(np.percentile(lat, 50)),
+                             "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
+                             "median_rel_gap": float(np.median(gaps))},
+            "fp64_one_at_a_time": {"requests": nf, "solves_per_s": nf / finish[-1],
+                                   "p50_s": float(np.percentile(lat64, 50)),
+                                   "p99_s": float(np.percentile(lat64, 99)),
+                                   "mean_solve_s": float(np.mean(solve_s))}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.serving:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

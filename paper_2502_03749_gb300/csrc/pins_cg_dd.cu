@@ -327,8 +327,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     gather3(buf, gam, dlt, rr);
     if (it == 0) bb = rr;
     if (!(bb > 0.f) || !(rr > a.rtol2 * bb) || it >= a.max_iter) break;   // NaN stops
-    const float beta = (it == 0) ? 0.f : gam / gam_prev;
-    const float alpha = (it == 0) ? gam / dlt : gam / (dlt - beta * gam / alpha_prev);
+    // the step lengths only steer the iteration (r and x stay consistent for any
+    // value), so the fast FP32 division is enough
+    const float beta = (it == 0) ? 0.f : __fdividef(gam, gam_prev);
+    const float alpha = (it == 0) ? __fdividef(gam, dlt)
+                                  : __fdividef(gam, dlt - beta * __fdividef(gam, alpha_prev));
     spmv(mg + (size_t)buf * N);
     // two unknowns per step, loads first, so their dependency chains overlap
     for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
