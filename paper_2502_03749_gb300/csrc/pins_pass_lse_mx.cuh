@@ -92,9 +92,28 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
   // log2(e) B_j = G_j log2(e) / eta as a pair (integer split of the FP64 G_j)
   for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = ddv_mul(split_f64(p.G[j], 0), p.l2e_eta);
   __syncthreads();
+  // full 1024-column segments of a dense cost: the whole row segment of a lane
+  // (8 chunks of 4) is loaded before any update, 8 16-byte loads in flight
+  const bool full8 = std::is_same<P, PolMixed<COST_DENSE>>::value && (n & 3) == 0 &&
+                     j1 - j0 == 8 * 128;
   for (int i = y * PINS_WARPS + warp; i < m; i += GY * PINS_WARPS) {
     float M = -INFINITY, S = 0.f;
     int jb = j0 + 4 * lane;
+    if (full8) {
+      float4 cv[8];
+      const float* row = p.cost.C32 + (size_t)i * n;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cv[k] = __ldg(reinterpret_cast<const float4*>(row + jb + 128 * k));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float c[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+        float wh[4], wl[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dd_w(sB[jb + 128 * k + q - j0], c[q], kh, kl, wh[q], wl[q]);
+        lse2_chunk(M, S, wh, wl);
+      }
+      jb = j1;                                      // segment done
+    }
     // two chunks of 4 per step: both loads issued before either update
     for (; jb + 128 + 3 < j1; jb += 256) {
       float c0[4], c1[4];
