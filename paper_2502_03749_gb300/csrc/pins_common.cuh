@@ -218,6 +218,54 @@ __device__ __forceinline__ dd dd_expm1(float th, float tl, const float2* __restr
 }
 
 // ------------------------------------------------------------------------- //
+// Bulk asynchronous copies (TMA engine) from global to shared memory, completed
+// on a shared-memory mbarrier.  Addresses 16-byte aligned, sizes multiples of 16.
+// ------------------------------------------------------------------------- //
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// orders shared-memory accesses of the threads (generic proxy) before later
+// accesses of the copy engine (async proxy)
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// makes barrier initialisations visible before their first use
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned int bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after `limit` polls (the caller records the failure)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned int parity,
+                                                  unsigned int limit) {
+  for (unsigned int k = 0; k < limit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ------------------------------------------------------------------------- //
 // warp / block reductions
 // ------------------------------------------------------------------------- //
 // double-float butterfly sum (every lane gets the total; fixed order)
@@ -367,6 +415,7 @@ struct PassArgs {
   dd kappa2_dd;                           // log2(e) kappa_dd
   const double* a; const double* b;
   const float2* exp_table;                // 2^(q/1024) pairs (mixed)
+  int* err;                               // bit 4: a bulk-copy wait gave up (may be NULL)
 };
 
 // Geometry of the tiled passes.

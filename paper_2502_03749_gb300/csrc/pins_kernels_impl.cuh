@@ -29,7 +29,11 @@ template <int K> struct Launch {
       // row groups for ~4 CTAs per SM (at most PINS_ROW_GROUPS counters)
       const int sx = std::max(1, std::min(g.gx, (p.n + 1023) / 1024));
       const int seg = (((p.n + sx - 1) / sx) + PINS_TC - 1) / PINS_TC * PINS_TC;
-      const size_t smem = sizeof(float2) * (size_t)seg;
+      // dense 1024-column segments stream through per-warp bulk-copy buffers
+      // (2 x 4 KB per warp): 3 CTAs per SM then
+      const bool bulk = P::MIXED && K == COST_DENSE && (p.n % 4) == 0 && seg == 1024 &&
+                        (reinterpret_cast<uintptr_t>(p.cost.C32) % 16) == 0;
+      const size_t smem = sizeof(float2) * (size_t)seg + (bulk ? 2u * 4096u * PINS_WARPS : 0u);
       if (smem <= PINS_ROW_SEG_SMEM) {
         static bool configured = false;
         if (!configured) {
@@ -37,7 +41,8 @@ template <int K> struct Launch {
                                PINS_ROW_SEG_SMEM);
           configured = true;
         }
-        const int gy = std::max(1, std::min({(4 * sm_count() + sx - 1) / sx, PINS_ROW_GROUPS,
+        const int per_sm = bulk ? 3 : 4;
+        const int gy = std::max(1, std::min({(per_sm * sm_count() + sx - 1) / sx, PINS_ROW_GROUPS,
                                              (p.m + PINS_WARPS - 1) / PINS_WARPS}));
         k_row_lse_mx<P><<<dim3(sx, gy), PINS_TPB, smem, st>>>(p, seg, ws, F_out, out_res);
         return;

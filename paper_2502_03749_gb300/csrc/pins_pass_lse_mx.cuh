@@ -80,10 +80,11 @@ __device__ __forceinline__ void cost4(const PassArgs& p, int i, int j, int jend,
 }
 
 template <class P>
-__global__ void __launch_bounds__(PINS_TPB)
+__global__ void __launch_bounds__(PINS_TPB, 2)
 k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
-  extern __shared__ float2 sB[];
+  extern __shared__ __align__(16) float2 sB[];
   __shared__ double sh_red[PINS_WARPS];
+  __shared__ unsigned long long s_bar[PINS_WARPS][2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int m = p.m, n = p.n;
   const int x = blockIdx.x, y = blockIdx.y, SX = gridDim.x, GY = gridDim.y;
@@ -92,28 +93,66 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
   // log2(e) B_j = G_j log2(e) / eta as a pair (integer split of the FP64 G_j)
   for (int j = j0 + threadIdx.x; j < j1; j += PINS_TPB) sB[j - j0] = ddv_mul(split_f64(p.G[j], 0), p.l2e_eta);
   __syncthreads();
-  // full 1024-column segments of a dense cost: the whole row segment of a lane
-  // (8 chunks of 4) is loaded before any update, 8 16-byte loads in flight
+  // full 1024-column segments of a dense cost: every warp streams its row
+  // segments (4 KB each) through two shared-memory buffers with bulk async
+  // copies, the next row's copy in flight while the current row is reduced
   const bool full8 = std::is_same<P, PolMixed<COST_DENSE>>::value && (n & 3) == 0 &&
-                     j1 - j0 == 8 * 128;
-  for (int i = y * PINS_WARPS + warp; i < m; i += GY * PINS_WARPS) {
-    float M = -INFINITY, S = 0.f;
-    int jb = j0 + 4 * lane;
-    if (full8) {
-      float4 cv[8];
-      const float* row = p.cost.C32 + (size_t)i * n;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) cv[k] = __ldg(reinterpret_cast<const float4*>(row + jb + 128 * k));
+                     seg == 8 * 128 && j1 - j0 == 8 * 128 &&
+                     (reinterpret_cast<uintptr_t>(p.cost.C32) & 15u) == 0;
+  if (full8) {
+    float* wbuf = reinterpret_cast<float*>(sB + seg) + warp * 2 * 1024;
+    if (threadIdx.x == 0) {
+      for (int w = 0; w < PINS_WARPS; ++w) { mbar_init(&s_bar[w][0], 1); mbar_init(&s_bar[w][1], 1); }
+      fence_mbar_init();
+      fence_proxy_async();
+    }
+    __syncthreads();
+    const int i_first = y * PINS_WARPS + warp, stride = GY * PINS_WARPS;
+    const int T = (i_first < m) ? (m - i_first + stride - 1) / stride : 0;
+    if (lane == 0 && T > 0) {
+      mbar_expect_tx(&s_bar[warp][0], 4096u);
+      bulk_g2s(wbuf, p.cost.C32 + (size_t)i_first * n + j0, 4096u, &s_bar[warp][0]);
+    }
+    bool ok = true;
+    for (int t = 0; t < T; ++t) {
+      const int i = i_first + t * stride;
+      if (lane == 0 && t + 1 < T) {     // the buffer of row t - 1 was released by __syncwarp
+        fence_proxy_async();
+        mbar_expect_tx(&s_bar[warp][(t + 1) & 1], 4096u);
+        bulk_g2s(wbuf + ((t + 1) & 1) * 1024, p.cost.C32 + (size_t)(i + stride) * n + j0, 4096u,
+                 &s_bar[warp][(t + 1) & 1]);
+      }
+      // a wait that gives up (never expected) is recorded; later rows then skip
+      // their waits so the pass still ends
+      if (ok && !mbar_wait_bounded(&s_bar[warp][t & 1], (unsigned int)((t >> 1) & 1), 1u << 22))
+        ok = false;
+      const float* rowbuf = wbuf + (t & 1) * 1024;
+      float M = -INFINITY, S = 0.f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float c[4] = {cv[k].x, cv[k].y, cv[k].z, cv[k].w};
+        const int col = 4 * lane + 128 * k;
+        const float4 cv = *reinterpret_cast<const float4*>(rowbuf + col);
         float wh[4], wl[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dd_w(sB[jb + 128 * k + q - j0], c[q], kh, kl, wh[q], wl[q]);
+        dd_w(sB[col + 0], cv.x, kh, kl, wh[0], wl[0]);
+        dd_w(sB[col + 1], cv.y, kh, kl, wh[1], wl[1]);
+        dd_w(sB[col + 2], cv.z, kh, kl, wh[2], wl[2]);
+        dd_w(sB[col + 3], cv.w, kh, kl, wh[3], wl[3]);
         lse2_chunk(M, S, wh, wl);
       }
-      jb = j1;                                      // segment done
+      __syncwarp();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float Mo = __shfl_xor_sync(0xffffffffu, M, o);
+        const float So = __shfl_xor_sync(0xffffffffu, S, o);
+        lse2_merge(M, S, Mo, So);
+      }
+      if (lane == 0) store_f2(ws.rowpart0 + (size_t)x * m + i, M, S);
     }
+    if (!ok && p.err) atomicOr(p.err, 16);
+  }
+  for (int i = y * PINS_WARPS + warp; !full8 && i < m; i += GY * PINS_WARPS) {
+    float M = -INFINITY, S = 0.f;
+    int jb = j0 + 4 * lane;
     // two chunks of 4 per step: both loads issued before either update
     for (; jb + 128 + 3 < j1; jb += 256) {
       float c0[4], c1[4];

@@ -404,6 +404,7 @@ PassArgs Solver::args(double s, const double* F, const double* G) {
   a.kappa2_dd.lo = (float)(k2 - (double)a.kappa2_dd.hi);
   a.a = a_; a.b = b_;
   a.exp_table = exp_table_;
+  a.err = reinterpret_cast<int*>(ws_.scal + SC_FLAG);
   return a;
 }
 
@@ -572,6 +573,8 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
   cudaMemcpyAsync(ws_.ab, a_, sizeof(double) * m, cudaMemcpyDeviceToDevice, stream_);
   cudaMemcpyAsync(ws_.ab + m, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, stream_);
   cudaMemsetAsync(ws_.scal + SC_FAST, 0, sizeof(FastSelState), stream_);
+  // error flags of the kernels (CG index check, bulk-copy waits); any bit is fatal
+  cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);
   // one-pass selection between the Newton steps of an outer iteration (mixed path)
   const bool fast_path = mixed_ && cfg.sparsify_one_pass != 0 && ps_->fast_collect != nullptr &&
                          2 * keep <= PINS_FAST_CAP;
@@ -620,7 +623,6 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         tau_prev = (float)reinterpret_cast<const SparsifyState*>(h_scal_ + SC_STATE)->tau;
         fast_ok = fast_path;
       }
-      cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // CG index-check flag
       // M d = grad with grad = (a - r; b - c); also <grad, d> and <ab, d> for the line search
       cudaError_t ce = run_cg(mixed_, m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
                               ws_.sw.data, nullptr, ws_.dir, cfg.cg_rtol, max_cg,
@@ -662,8 +664,9 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
           int flag = 0;
           std::memcpy(&flag, h_scal_ + SC_FLAG, sizeof(int));
           if (flag) {
-            err_ = "cg: an index outside the cluster's slices was skipped (flag " +
-                   std::to_string(flag) + ")";
+            err_ = std::string((flag & 16) ? "a bulk-copy wait gave up in a Sinkhorn pass"
+                                           : "cg: an index outside the cluster's slices was skipped") +
+                   " (flag " + std::to_string(flag) + ")";
             r.status = PINS_ERR_CUDA;
             return PINS_ERR_CUDA;
           }

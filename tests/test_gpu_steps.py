@@ -74,6 +74,31 @@ def test_sinkhorn_half_steps(handles, prec, m, n):
                                atol=1e-14 if prec == "fp64" else 2e-7)
 
 
+@pytest.mark.parametrize("m,n", [(300, 2048), (1030, 4096)])
+def test_sinkhorn_bulk_copy_segments(handles, m, n):
+    """Dense FP32 costs whose width is a multiple of 1024 take the row pass that
+    streams each row segment through shared memory with bulk async copies."""
+    C, a, b, F, G, eta, s = random_state(m, n, m + 3 * n)
+    F = F * 0.0; G = G * 0.0
+    h = handles["mixed"]
+    prob = dense_device_problem(C.astype(np.float32), a, b)
+    Fd, Gd = dev(F), dev(G)
+    rr = torch_zeros(3)
+    st = pins.pins_step_sinkhorn(h.h, prob.prob, s, 3, Fd, Gd, rr)
+    assert st == 0, h.error()
+    Fo, Go = F.copy(), G.copy()
+    for _ in range(3):
+        Fo, _ = po.sinkhorn_row_step(C, a, Fo, Go, eta, s)
+        Go = po.sinkhorn_col_step(C, b, Fo, Go, eta, s)
+    np.testing.assert_allclose(Fd.cpu().numpy(), Fo, atol=2e-6 * eta, rtol=0)
+    np.testing.assert_allclose(Gd.cpu().numpy(), Go, atol=2e-6 * eta, rtol=0)
+
+
+def torch_zeros(k):
+    import torch
+    return torch.zeros(k, dtype=torch.float64, device="cuda")
+
+
 def _tie_state(m, n, seed):
     rng = np.random.default_rng(seed)
     C = rng.integers(0, 3, size=(m, n)).astype(np.float64) / 4.0
