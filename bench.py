@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="plain FP64 solves timed for the comparison key (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--lse-roofline", type=int, default=0, metavar="N",
+                    help="instead of the contract line: HBM roofline of the mixed Sinkhorn "
+                         "row and column passes on an N x N dense FP32 GMM cost (N = 16384 "
+                         "puts C at 1 GiB, well beyond L2)")
     ap.add_argument("--serving", action="store_true",
                     help="instead of the contract line: a served request stream (Poisson "
                          "arrivals of point-cloud pairs) with p50/p99 latency, mixed served vs "
@@ -458,7 +462,7 @@ def run_serving(args):
         t_prev = max(t_prev, arr[i]) + dt
         finish.append(t_prev)
     h64.close()
-    lat64 = np.array([finish[i] - arr[i] for i in range(nf)])
+    lat64 = np.array([finish[i] - arr[i] for i in range(nf)]) if nf else np.zeros(1)
     ns = [r.prob.n for r in refs]
     line = {"mode": "serving", "metric": "OT solves/s + p50/p99 latency", "unit": "solves/s",
             "requests": R, "rate_per_s": args.serve_rate,
@@ -469,15 +473,52 @@ def run_serving(args):
             "mixed_served": {"solves_per_s": R / span, "p50_s": float(np.percentile(lat, 50)),
                              "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
                              "median_rel_gap": float(np.median(gaps))},
-            "fp64_one_at_a_time": {"requests": nf, "solves_per_s": nf / finish[-1],
+            "fp64_one_at_a_time": None if nf == 0 else {"requests": nf, "solves_per_s": nf / finish[-1],
                                    "p50_s": float(np.percentile(lat64, 50)),
                                    "p99_s": float(np.percentile(lat64, 99)),
                                    "mean_solve_s": float(np.mean(solve_s))}}
     print(json.dumps(line), flush=True)
 
 
+def run_lse_roofline(args):
+    """Times the mixed Sinkhorn half-steps (one row and one column pass per
+    iteration, each reading the dense FP32 C once) with the library's per-class
+    CUDA events, and reports achieved GB/s against the measured HBM copy rate."""
+    import torch
+    from paper_2502_03749_gb300 import pins, workloads as wl
+    n = args.lse_roofline
+    w = wl.gmm_instance(0, m=n, n=n, eta=args.eta)
+    C = torch.from_numpy(w.dense_cost().astype(np.float32)).cuda()
+    a = torch.from_numpy(w.a).cuda(); b = torch.from_numpy(w.b).cuda()
+    prob = pins.make_problem("dense", a, b, C=C, on_device=True)
+    h = pins.Pins(prec="mixed", eta=args.eta, profile=1)
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    G = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s = 50.0                                   # a mid-solve scale s/eta
+    pins.pins_step_sinkhorn(h.h, prob.prob, s, 3, F, G, None)      # warm-up
+    torch.cuda.synchronize()
+    pins.pins_profile_read(h.h, reset=True)
+    iters = max(3, args.steps * 5)
+    pins.pins_step_sinkhorn(h.h, prob.prob, s, iters, F, G, None)
+    torch.cuda.synchronize()
+    prof = pins.pins_profile_read(h.h, reset=True)
+    h.close()
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    out = {"mode": "lse_roofline", "n": n, "bytes_per_pass": 4 * n * n, "iterations": iters}
+    for k in ("row_lse", "col_lse"):
+        ms, cnt = prof[k]
+        t = ms / cnt / 1e3
+        gbs = 4.0 * n * n / t / 1e9
+        out[k] = {"us_per_pass": t * 1e6, "achieved_gbs": gbs, "peak_gbs": peak,
+                  "frac": gbs / peak}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.lse_roofline:
+        run_lse_roofline(args)
+        return
     if args.serving:
         run_serving(args)
         return
