@@ -45,6 +45,12 @@ def parse():
                     help="instead of the contract line: HBM roofline of the mixed Sinkhorn "
                          "row and column passes on an N x N dense FP32 GMM cost (N = 16384 "
                          "puts C at 1 GiB, well beyond L2)")
+    ap.add_argument("--batch", type=int, default=0, metavar="P",
+                    help="instead of the contract line: P stroke-histogram pairs (grids 16^2 to "
+                         "64^2) through pins_solve_batch, mixed, vs plain FP64 one at a time")
+    ap.add_argument("--batch-inflight", type=int, default=8)
+    ap.add_argument("--fp64-seconds", type=float, default=120.0,
+                    help="time budget of the FP64 one-at-a-time arm of --batch")
     ap.add_argument("--serving", action="store_true",
                     help="instead of the contract line: a served request stream (Poisson "
                          "arrivals of point-cloud pairs) with p50/p99 latency, mixed served vs "
@@ -480,6 +486,46 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """P stroke-histogram pairs (1-3 thick polylines, shifted or rotated, grids
+    drawn from 16^2 ... 64^2, squared pixel distance / max) solved by one
+    pins_solve_batch call (instances run concurrently, batch_inflight at a time),
+    against plain FP64 PINS one pair at a time within a time budget."""
+    import torch
+    from paper_2502_03749_gb300 import pins, workloads as wl
+    P = args.batch
+    refs = [pins.problem_from_workload(wl.stroke_pair(i, eta=args.eta)) for i in range(P)]
+    common = dict(eta=args.eta, K=args.K)
+    hw = pins.Pins(prec="mixed", **common)
+    hw.solve(refs[0]); hw.close()                    # warm-up
+    h = pins.Pins(prec="mixed", max_inflight=args.batch_inflight, **common)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = h.solve_batch(refs)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    h.close()
+    h64 = pins.Pins(prec="fp64", **common)
+    n64, t64, diffs = 0, 0.0, []
+    for i in range(P):
+        if t64 > args.fp64_seconds:
+            break
+        ts = time.perf_counter()
+        d = h64.solve(refs[i], want_potentials=False)
+        t64 += time.perf_counter() - ts
+        n64 += 1
+        diffs.append(abs(outs[i]["cost"] - d["cost"]) / abs(d["cost"]))
+    h64.close()
+    sizes = [r.prob.n for r in refs]
+    line = {"mode": "batch", "metric": "OT solves/s", "unit": "solves/s", "pairs": P,
+            "grid_sizes": sorted(set(sizes)), "config": {"eta": args.eta, "K": args.K,
+                                                         "inflight": args.batch_inflight},
+            "mixed_batch": {"solves_per_s": P / tb, "seconds": tb},
+            "fp64_one_at_a_time": {"pairs": n64, "solves_per_s": n64 / t64 if t64 else None,
+                                   "max_rel_cost_diff_vs_mixed": max(diffs) if diffs else None}}
+    print(json.dumps(line), flush=True)
+
+
 def run_lse_roofline(args):
     """Times the mixed Sinkhorn half-steps (one row and one column pass per
     iteration, each reading the dense FP32 C once) with the library's per-class
@@ -518,6 +564,9 @@ def main():
     args = parse()
     if args.lse_roofline:
         run_lse_roofline(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
     if args.serving:
         run_serving(args)

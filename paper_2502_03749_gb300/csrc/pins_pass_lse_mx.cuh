@@ -73,6 +73,36 @@ __device__ __forceinline__ void cost4(const PassArgs& p, int i, int j, int jend,
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) c[q] = (j + q < jend) ? __ldg(row + j + q) : 0.f;
+  } else if constexpr (std::is_same<P, PolMixed<COST_GRID>>::value) {
+    // grid cost: one division per row and per chunk; consecutive columns step
+    // along the grid row (integers exact in FP32)
+    const int s2 = p.cost.s2;
+    const int i1 = i / s2, i2 = i - i1 * s2;
+    int j1 = j / s2, j2 = j - j1 * s2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int d1 = i1 - j1, d2 = i2 - j2;
+      c[q] = (j + q < jend) ? (float)(d1 * d1 + d2 * d2) : 0.f;
+      if (++j2 == s2) { j2 = 0; ++j1; }
+    }
+  } else if constexpr (std::is_same<P, PolMixed<COST_POINTS>>::value) {
+    if (p.cost.d == 2) {      // planar points: the row point once, 8-byte column points
+      const float2 xi = __ldg(reinterpret_cast<const float2*>(p.cost.xf) + i);
+      const float2* yv = reinterpret_cast<const float2*>(p.cost.yf);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (j + q < jend) {
+          const float2 yj = __ldg(yv + j + q);
+          const float d0 = xi.x - yj.x, d1 = xi.y - yj.y;
+          c[q] = __fmaf_rn(d1, d1, d0 * d0);
+        } else {
+          c[q] = 0.f;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] = (j + q < jend) ? P::cost(p, i, j + q) : 0.f;
+    }
   } else {
 #pragma unroll
     for (int q = 0; q < 4; ++q) c[q] = (j + q < jend) ? P::cost(p, i, j + q) : 0.f;
