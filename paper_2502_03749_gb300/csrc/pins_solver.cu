@@ -587,17 +587,51 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
     const double s = (double)(k + 1);
     cert_current = false;
     // ---- Sinkhorn warm-up (readings R3, R4) ----
+    // Blocks of check_every iterations (the residual of the block's last row
+    // half-step decides the early exit).  Unprofiled solves launch a full block
+    // as one CUDA graph, captured once per outer iteration (s is fixed within it).
     int t = 0;
+    cudaGraphExec_t gexec = nullptr;
+    long long glaunch = 0;                      // kernels in one graph launch
+    bool use_graph = !profile_ && check_every >= 2;
     while (t < cfg.T1) {
-      sinkhorn_iter(s, t);
-      ++t;
-      if (t % check_every == 0) {
-        cudaMemcpyAsync(h_scal_ + SC_ROWRES + t - 1, ws_.scal + SC_ROWRES + t - 1,
+      const int blk = std::min(check_every, cfg.T1 - t);
+      bool launched = false;
+      if (use_graph && blk == check_every) {
+        if (!gexec) {
+          cudaGraph_t graph = nullptr;
+          const long long l0 = launches_;
+          if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q);
+            if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess ||
+                cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
+              gexec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
+          }
+          glaunch = launches_ - l0;
+          launches_ = l0;
+          if (!gexec) { cudaGetLastError(); use_graph = false; }
+        }
+        if (gexec && cudaGraphLaunch(gexec, stream_) == cudaSuccess) {
+          launches_ += glaunch;
+          launched = true;
+        }
+      }
+      if (!launched)
+        for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q);
+      t += blk;
+      if (blk == check_every) {
+        cudaMemcpyAsync(h_scal_ + SC_ROWRES + blk - 1, ws_.scal + SC_ROWRES + blk - 1,
                         sizeof(double), cudaMemcpyDeviceToHost, stream_);
-        if ((stt = sync("warm-up")) != PINS_OK) { r.status = stt; return stt; }
-        if (h_scal_[SC_ROWRES + t - 1] <= tol) break;
+        if ((stt = sync("warm-up")) != PINS_OK) {
+          if (gexec) cudaGraphExecDestroy(gexec);
+          r.status = stt;
+          return stt;
+        }
+        if (h_scal_[SC_ROWRES + blk - 1] <= tol) break;
       }
     }
+    if (gexec) cudaGraphExecDestroy(gexec);
     r.sinkhorn_iters += t;
     // ---- sparse Newton (Alg. 2 second loop) ----
     prep(s);

@@ -138,6 +138,26 @@ def test_batch_and_serving_match_solo(prec):
         assert np.array_equal(s["F"], b["F"]) and np.array_equal(s["F"], v["F"])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_warmup_matches_direct_launches(prec):
+    """Unprofiled solves launch each block of Sinkhorn half-steps as one captured
+    CUDA graph; profiled solves launch the kernels one by one.  Both run the same
+    kernels on the same data, so the solves are bit-identical."""
+    w = wl.gmm_instance(1, m=200, n=176, eta=1e-2)
+    ref = pins.problem_from_workload(w)
+    out = []
+    for prof in (0, 1):
+        h = pins.Pins(prec=prec, eta=1e-2, K=3, tol_marg=1e-12, profile=prof)
+        try:
+            out.append(h.solve(ref))
+        finally:
+            h.close()
+    a, b = out
+    assert a["sinkhorn_iters"] == b["sinkhorn_iters"] >= 20
+    assert a["newton_iters"] == b["newton_iters"] and a["cost"] == b["cost"]
+    assert np.array_equal(a["F"], b["F"]) and np.array_equal(a["G"], b["G"])
+
+
 @pytest.mark.parametrize("case", ["gmm", "grid"])
 def test_one_pass_selection_matches_histogram_search(case):
     """The mixed path's one-pass selection (later Newton steps of an outer
