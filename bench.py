@@ -163,10 +163,13 @@ def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, mixed):
     potentials and partials are O(m + n)); bound 'hbm' against the measured copy
     bandwidth.  CG per iteration: FP64 path 4 nnz + 14 (m + n) FP64 flops
     (off-diagonal SpMV on the CSR and CSC copies, diagonal, three dot products and
-    four vector updates) against the nominal FP64 rate; mixed path the same
-    operations in double-float, 24 nnz + 60 (m + n) FP32 flops (a double-float
-    multiply-add is ~12 FP32 flops, FMA = 2), against the FP32 peak from the unit
-    counts and clock (152 SMs x 128 lanes x 2 x 2.07 GHz)."""
+    four vector updates) against the nominal FP64 rate; mixed path (pipelined
+    ordering, double-float vectors) counted as the FP32 operations the pipelined
+    kernel issues (FMA = 2): 15 per stored entry of the CSR and CSC copies (a
+    double-float product and compensated sum), 152 per unknown (eight
+    double-float axpy updates of 15, the diagonal product and sum, the Jacobi
+    scaling, three FP32 dot terms), i.e. 30 nnz + 152 (m + n), against the FP32
+    peak from the unit counts and clock (152 SMs x 128 lanes x 2 x 2.07 GHz)."""
     dom, (ms, cnt) = max(prof.items(), key=lambda kv: kv[1][0])
     if cnt == 0:
         return None, dom
@@ -174,7 +177,7 @@ def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, mixed):
     if dom == "cg":
         iters = cg_iters / max(cnt, 1)
         if mixed:
-            per_launch = (24.0 * nnz + 60.0 * (m + n)) * iters
+            per_launch = (30.0 * nnz + 152.0 * (m + n)) * iters
             peak, src = FP32_PEAK_TFLOPS, "FP32 units x clock (152 x 128 x 2 x 2.07 GHz)"
         else:
             per_launch = (4.0 * nnz + 14.0 * (m + n)) * iters
@@ -184,7 +187,7 @@ def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, mixed):
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": src, "avg_launch_us": t * 1e6, "launches": cnt,
                 "iters_per_launch": iters,
-                "note": "latency-bound: two cluster barriers per CG iteration"}, dom
+                "note": "latency-bound: one cluster barrier and one L2 exchange per CG iteration"}, dom
     per_launch = float(m) * n * elem_bytes
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch / t / 1e9
