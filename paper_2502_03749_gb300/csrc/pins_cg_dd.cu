@@ -23,7 +23,9 @@
 // In exact arithmetic these are the iterates, and the iteration count, of the
 // textbook Jacobi PCG with the same stopping rule.  The m slices go through L2
 // (two alternating buffers, so one barrier per iteration suffices), the block
-// partials through distributed shared memory (two alternating slot sets).
+// partials through distributed shared memory (two alternating slot sets).  A
+// system small enough for one CTA runs in a cluster of one, which reads m from
+// its own shared memory.
 // Every CTA sums the block partials in the same order and takes the same
 // decisions, so results are reproducible run to run.
 #include <cooperative_groups.h>
@@ -37,6 +39,13 @@ namespace pins {
 #define PINS_DDCG_MAX 16
 #define PINS_DDCG_TPB 256
 #define PINS_DDCG_SMEM (200 * 1024)
+// cluster size: one CTA up to PINS_DDCG_LOCAL_MAX unknowns (no exchange through
+// L2, no cluster barrier), else at most PINS_DDCG_SLICE unknowns per CTA where
+// the cluster size allows.  Measured on GB300: a 1-CTA CG on 512 unknowns takes
+// 3.7 us per iteration against 3.9-5.7 us for 2-16 CTAs; on 2048 unknowns 8 CTAs
+// (4.1 us) beat 4 (4.5 us) and 16 (4.5 us); on 8192, 16 CTAs (5.9 us) beat 8 (7.1 us).
+#define PINS_DDCG_LOCAL_MAX 512
+#define PINS_DDCG_SLICE 256
 // shared bytes per unknown: x, r, u, w, z, q, s, p, m, diag, od (11 x 8) + D^-1 (4) + row begin (4)
 #define PINS_DDCG_PER_UNKNOWN 96
 
@@ -57,6 +66,9 @@ struct CGddArgs {
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
 };
 
+// LOCAL: a cluster of one CTA holds every unknown, so the SpMV reads m from its
+// own shared memory and nothing goes through the exchange buffer.
+template <bool LOCAL>
 __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     const float2 u0 = ddv_scale(dinv[k], r0);
     uv[k] = u0;
     mv[k] = u0;
-    __stcg(mg + N + lo + k, u0);
+    if (!LOCAL) __stcg(mg + N + lo + k, u0);
   }
   // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
   const int ne = E1 - E0;
@@ -214,7 +226,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
           rw[q] = ok ? erow[base + q] : cur;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) uu[q] = __ldcg(src + tg[q]);
+        for (int q = 0; q < 4; ++q) uu[q] = LOCAL ? mv[tg[q]] : __ldcg(src + tg[q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           two_prod(v[q].x, uu[q].x, ph[q], pl[q]);
@@ -318,7 +330,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
       lrr = __fmaf_rn(rk, rk, lrr);
       const float2 mk = ddv_scale(dinv[k], w);
       mv[k] = mk;
-      __stcg(mg + (size_t)buf * N + lo + k, mk);
+      if (!LOCAL) __stcg(mg + (size_t)buf * N + lo + k, mk);
     }
     publish3(lg, ld, lrr, buf);
     cluster.sync();                                 // m slices and partials published
@@ -407,12 +419,15 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   }
 }
 
-static int ddcg_cluster_size() {
+// largest cluster the device runs with this kernel's shared memory: 16 CTAs
+// (non-portable size) where available, else 8
+static int ddcg_max_cluster() {
   static int cs = 0;
   if (cs) return cs;
-  cudaFuncSetAttribute(k_pcg_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
+  cudaFuncSetAttribute(k_pcg_dd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
+  cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
   cs = 8;
-  if (cudaFuncSetAttribute(k_pcg_dd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+  if (cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
       cudaSuccess) {
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(16);
@@ -423,7 +438,8 @@ static int ddcg_cluster_size() {
     attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
     lc.attrs = attr; lc.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_dd, &lc) == cudaSuccess && nclusters >= 1)
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_dd<false>, &lc) == cudaSuccess &&
+        nclusters >= 1)
       cs = 16;
   }
   cudaGetLastError();
@@ -435,6 +451,17 @@ size_t ddcg_smem_bytes(int N, int cs) {
   return (size_t)PINS_DDCG_PER_UNKNOWN * L4 + 16;
 }
 
+// cluster size for N unknowns (a power of two up to maxcs), with at least as
+// many CTAs as the shared memory needs
+static int ddcg_cluster_for(int N, int maxcs) {
+  if (N <= PINS_DDCG_LOCAL_MAX && ddcg_smem_bytes(N, 1) <= PINS_DDCG_SMEM) return 1;
+  int cs = 2;
+  while (cs < maxcs && ((N + cs - 1) / cs > PINS_DDCG_SLICE ||
+                        ddcg_smem_bytes(N, cs) > PINS_DDCG_SMEM))
+    cs *= 2;
+  return cs;
+}
+
 cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
@@ -443,7 +470,7 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
                           int max_iter, double* info, int* flag, cudaStream_t st, bool* used) {
   *used = false;
   const int N = m + n;
-  const int CS = ddcg_cluster_size();
+  const int CS = ddcg_cluster_for(N, ddcg_max_cluster());
   const int L = (N + CS - 1) / CS;
   if (ddcg_smem_bytes(N, CS) > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
   const size_t smem = PINS_DDCG_SMEM;   // the rest holds a copy of u and the entries when they fit
@@ -467,7 +494,8 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
   lc.attrs = attr;
   lc.numAttrs = 1;
   *used = true;
-  return cudaLaunchKernelEx(&lc, k_pcg_dd, a);
+  return CS == 1 ? cudaLaunchKernelEx(&lc, k_pcg_dd<true>, a)
+                 : cudaLaunchKernelEx(&lc, k_pcg_dd<false>, a);
 }
 
 }  // namespace pins

@@ -243,11 +243,14 @@ def test_step_rejects_host_pointers(handles):
 
 
 @pytest.mark.parametrize("m,n,rtol", [(70, 150, 1e-10), (40, 40, 1e-10), (1, 9, 1e-10),
+                                      (256, 256, 1e-9), (200, 313, 1e-9), (430, 590, 1e-9),
                                       (700, 1500, 1e-6), (1234, 777, 1e-9)])
 def test_cg_double_float_matches_dense_solve(handles, m, n, rtol):
     """The mixed handle runs the CG in double-float arithmetic with FP32 inner
     products: M d must still reproduce rhs to the requested relative residual,
-    and the iteration count stays close to the FP64 oracle's."""
+    and the iteration count stays close to the FP64 oracle's.  The sizes cover
+    every cluster size: one CTA (up to 512 unknowns, 512 included), 4 CTAs (513
+    and 1020 unknowns), 8 (2011) and 16 (2200)."""
     import torch
     C, a, b, F, G, eta, s = random_state(m, n, 7 * m + n)
     ga, gb, r, c = po.gradient(C, a, b, F, G, eta, s)
