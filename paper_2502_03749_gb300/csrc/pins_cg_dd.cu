@@ -310,28 +310,31 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     t0r = q0; t1r = q1; t2r = q2;
   };
 
-  // w0 = M u0
+  // (r.u, w.u, r.r) partials and m = D^-1 w of the own unknown k, m published in
+  // exchange buffer b (the next iteration's phase A, fused into the vector updates)
+  auto phase_a = [&](int k, float2 w, float rk, float uk, int b, float& lg, float& ld,
+                     float& lrr) {
+    lg = __fmaf_rn(rk, uk, lg);
+    ld = __fmaf_rn(w.x, uk, ld);
+    lrr = __fmaf_rn(rk, rk, lrr);
+    const float2 mk = ddv_scale(dinv[k], w);
+    mv[k] = mk;
+    if (!LOCAL) __stcg(mg + (size_t)b * N + lo + k, mk);
+  };
+
+  // w0 = M u0, then phase A of the first iteration
   cluster.sync();                                   // every u0 slice published
   spmv(mg + N);
-  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-    wv[k] = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
-    od[k] = make_float2(0.f, 0.f);
-  }
   int it = 0, buf = 0;
+  float lg = 0.f, ld = 0.f, lrr = 0.f;
+  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+    const float2 w = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
+    wv[k] = w;
+    od[k] = make_float2(0.f, 0.f);
+    phase_a(k, w, rv[k].x, uv[k].x, buf, lg, ld, lrr);
+  }
   float gam_prev = 1.f, alpha_prev = 1.f, bb = 0.f, rr = 0.f;
   while (true) {
-    // phase A (own unknowns): (r.u, w.u, r.r) partials; m = D^-1 w published
-    float lg = 0.f, ld = 0.f, lrr = 0.f;
-    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-      const float2 w = wv[k];
-      const float rk = rv[k].x, uk = uv[k].x;
-      lg = __fmaf_rn(rk, uk, lg);
-      ld = __fmaf_rn(w.x, uk, ld);
-      lrr = __fmaf_rn(rk, rk, lrr);
-      const float2 mk = ddv_scale(dinv[k], w);
-      mv[k] = mk;
-      if (!LOCAL) __stcg(mg + (size_t)buf * N + lo + k, mk);
-    }
     publish3(lg, ld, lrr, buf);
     cluster.sync();                                 // m slices and partials published
     // phase B: scalars (identical in every CTA), then n = M m
@@ -345,7 +348,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     const float alpha = (it == 0) ? __fdividef(gam, dlt)
                                   : __fdividef(gam, dlt - beta * __fdividef(gam, alpha_prev));
     spmv(mg + (size_t)buf * N);
-    // two unknowns per step, loads first, so their dependency chains overlap
+    // two unknowns per step, loads first, so their dependency chains overlap;
+    // phase A of the next iteration follows each unknown's update (the same
+    // summation order as a separate pass over k = tid, tid + TPB, ...)
+    const int nb = buf ^ 1;
+    lg = 0.f; ld = 0.f; lrr = 0.f;
     for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
       const int k2 = k + PINS_DDCG_TPB;
       const bool two = k2 < nl;
@@ -376,12 +383,13 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
         od[t] = make_float2(0.f, 0.f);
         zv[t] = z0[h]; qv[t] = q0[h]; sv[t] = s0[h]; pv[t] = p0[h];
         xv[t] = x0[h]; rv[t] = r0[h]; uv[t] = u0[h]; wv[t] = w0[h];
+        phase_a(t, w0[h], r0[h].x, u0[h].x, nb, lg, ld, lrr);
       }
     }
     gam_prev = gam;
     alpha_prev = alpha;
     ++it;
-    buf ^= 1;
+    buf = nb;
   }
   const double scale = ldexp(1.0, shift);
   double dg0 = 0.0, dg1 = 0.0;                      // <rhs, x>, <ab, x> partials
