@@ -250,26 +250,30 @@ __global__ void __launch_bounds__(PINS_CGC_TPB) k_pcg_cg1(CGClusterArgs a) {
   cluster.sync();                                   // no CTA exits while others read its u
 }
 
+// 16 CTAs (non-portable cluster size) where the device runs them with this
+// kernel's shared memory, else 8; decided once, thread-safely
 static int cg1_cluster_size() {
-  static int cs = 0;
-  if (cs) return cs;
-  cudaFuncSetAttribute(k_pcg_cg1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cs = 8;
-  if (cudaFuncSetAttribute(k_pcg_cg1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-      cudaSuccess) {
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(16);
-    lc.blockDim = dim3(PINS_CGC_TPB);
-    lc.dynamicSmemBytes = 200 * 1024;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    lc.attrs = attr; lc.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_cg1, &lc) == cudaSuccess && nclusters >= 1)
-      cs = 16;
-  }
-  cudaGetLastError();
+  static const int cs = [] {
+    cudaFuncSetAttribute(k_pcg_cg1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int v = 8;
+    if (cudaFuncSetAttribute(k_pcg_cg1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(16);
+      lc.blockDim = dim3(PINS_CGC_TPB);
+      lc.dynamicSmemBytes = 200 * 1024;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+      lc.attrs = attr; lc.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_cg1, &lc) == cudaSuccess &&
+          nclusters >= 1)
+        v = 16;
+    }
+    cudaGetLastError();
+    return v;
+  }();
   return cs;
 }
 

@@ -428,29 +428,33 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
 }
 
 // largest cluster the device runs with this kernel's shared memory: 16 CTAs
-// (non-portable size) where available, else 8
+// (non-portable size) where available, else 8; decided once, thread-safely, so
+// that concurrent solves of one size always use the same cluster size
 static int ddcg_max_cluster() {
-  static int cs = 0;
-  if (cs) return cs;
-  cudaFuncSetAttribute(k_pcg_dd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
-  cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_DDCG_SMEM);
-  cs = 8;
-  if (cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-      cudaSuccess) {
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(16);
-    lc.blockDim = dim3(PINS_DDCG_TPB);
-    lc.dynamicSmemBytes = PINS_DDCG_SMEM;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-    lc.attrs = attr; lc.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_dd<false>, &lc) == cudaSuccess &&
-        nclusters >= 1)
-      cs = 16;
-  }
-  cudaGetLastError();
+  static const int cs = [] {
+    cudaFuncSetAttribute(k_pcg_dd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PINS_DDCG_SMEM);
+    cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         PINS_DDCG_SMEM);
+    int v = 8;
+    if (cudaFuncSetAttribute(k_pcg_dd<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t lc = {};
+      lc.gridDim = dim3(16);
+      lc.blockDim = dim3(PINS_DDCG_TPB);
+      lc.dynamicSmemBytes = PINS_DDCG_SMEM;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+      lc.attrs = attr; lc.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_pcg_dd<false>, &lc) == cudaSuccess &&
+          nclusters >= 1)
+        v = 16;
+    }
+    cudaGetLastError();
+    return v;
+  }();
   return cs;
 }
 

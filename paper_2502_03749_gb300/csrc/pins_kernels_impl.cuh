@@ -7,14 +7,16 @@
 namespace pins {
 namespace {
 
+// function-local statics below are initialised once, thread-safely (the serving
+// workers launch from several threads)
 int sm_count() {
-  static int v = 0;
-  if (!v) {
-    int d = 0;
+  static const int v = [] {
+    int d = 0, x = 0;
     cudaGetDevice(&d);
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
-      v = 148;
-  }
+    if (cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || x <= 0)
+      x = 152;
+    return x;
+  }();
   return v;
 }
 
@@ -35,12 +37,9 @@ template <int K> struct Launch {
                         (reinterpret_cast<uintptr_t>(p.cost.C32) % 16) == 0;
       const size_t smem = sizeof(float2) * (size_t)seg + (bulk ? 2u * 4096u * PINS_WARPS : 0u);
       if (smem <= PINS_ROW_SEG_SMEM) {
-        static bool configured = false;
-        if (!configured) {
-          cudaFuncSetAttribute(k_row_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               PINS_ROW_SEG_SMEM);
-          configured = true;
-        }
+        static const cudaError_t configured = cudaFuncSetAttribute(
+            k_row_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_ROW_SEG_SMEM);
+        (void)configured;
         const int per_sm = bulk ? 3 : 4;
         const int gy = std::max(1, std::min({(per_sm * sm_count() + sx - 1) / sx, PINS_ROW_GROUPS,
                                              (p.m + PINS_WARPS - 1) / PINS_WARPS}));
@@ -62,12 +61,9 @@ template <int K> struct Launch {
       const int rb = (p.m + gy - 1) / gy;
       const size_t smem = sizeof(float2) * (size_t)rb;
       if (smem <= PINS_ROW_SEG_SMEM) {
-        static bool configured = false;
-        if (!configured) {
-          cudaFuncSetAttribute(k_col_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               PINS_ROW_SEG_SMEM);
-          configured = true;
-        }
+        static const cudaError_t configured = cudaFuncSetAttribute(
+            k_col_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_ROW_SEG_SMEM);
+        (void)configured;
         k_col_lse_mx<P><<<dim3(g.gx, gy), PINS_TPB, smem, st>>>(p, rb, ws, G_out);
         return;
       }
@@ -81,14 +77,14 @@ template <int K> struct Launch {
       // groups for one wave at 2 CTAs per SM (at most g.gy: colpart holds g.gy * n)
       const int sx = (p.n + PINS_MSEG - 1) / PINS_MSEG;
       if (sx <= g.gx) {
-        static bool configured = false;
-        if (!configured) {
+        static const bool configured = [] {
           cudaFuncSetAttribute(k_marg_mx<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)PINS_MSEG_SMEM);
           cudaFuncSetAttribute(k_marg_mx<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)PINS_MSEG_SMEM);
-          configured = true;
-        }
+          return true;
+        }();
+        (void)configured;
         const int gy = std::max(1, std::min({(2 * sm_count() + sx - 1) / sx, g.gy,
                                              (p.m + PINS_WARPS - 1) / PINS_WARPS}));
         if (tr) {

@@ -109,13 +109,9 @@ void launch_key_select(SparsifyState* st, unsigned int* hist, long long, cudaStr
 cudaError_t launch_cand_select(SparsifyState* st, const double* cand_key,
                                const long long* cand_idx, int n, int* rowcnt, cudaStream_t s) {
   size_t smem = (size_t)PINS_CAND_CAP * (sizeof(double) + sizeof(long long));
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_cand_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured =   // once, thread-safely
+      cudaFuncSetAttribute(k_cand_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (configured != cudaSuccess) return configured;
   k_cand_select<<<1, 1024, smem, s>>>(st, cand_key, cand_idx, n, rowcnt);
   return cudaGetLastError();
 }
@@ -237,13 +233,9 @@ cudaError_t launch_fast_select(FastSelState* fs, const float* ckey, const unsign
                                int K, cudaStream_t s) {
   const size_t smem = sizeof(unsigned int) * (PINS_FAST_CAP + 2048) +
                       sizeof(unsigned long long) * PINS_FAST_TIES;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_fast_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured =   // once, thread-safely
+      cudaFuncSetAttribute(k_fast_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (configured != cudaSuccess) return configured;
   k_fast_select<<<1, 1024, smem, s>>>(fs, ckey, cij, K);
   return cudaGetLastError();
 }
