@@ -138,6 +138,56 @@ def test_batch_and_serving_match_solo(prec):
         assert np.array_equal(s["F"], b["F"]) and np.array_equal(s["F"], v["F"])
 
 
+def test_sinkhorn_eppa_baseline_matches_oracle():
+    """Sinkhorn+EPPA, the paper's first comparison solver (Section 5.1), is PINS
+    with the Newton phase switched off (T2 = 0): the same kernels, and on the
+    FP64 path the same iterates as the oracle run with the same settings."""
+    w = wl.small_points(4, m=40, n=52)
+    kw = dict(eta=1e-2, tol_marg=1e-10, K=6, T2=0)
+    ref = po.pins(w.C, w.a, w.b, gamma=2.0, **kw)
+    out = _solve(pins.problem_from_workload(w), sparsify_gamma=2.0, **kw)
+    assert out["outer_iters"] == ref["outer_iters"] == 6
+    assert out["sinkhorn_iters"] == ref["sinkhorn_iters"] and out["newton_iters"] == 0
+    assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= 1e-10
+    np.testing.assert_allclose(out["F"], ref["F"], rtol=0, atol=1e-9 * np.abs(ref["F"]).max())
+
+
+def test_sinkhorn_without_eppa_matches_algorithm_1():
+    """Sinkhorn without EPPA is one outer iteration of Sinkhorn half-steps
+    (K = 1, T2 = 0): the plan at s = 1 is Algorithm 1's scaling form at
+    eps = eta, so the converged cost equals that of the oracle's separate
+    Algorithm 1 routine (a different residual schedule, the same unique
+    entropic optimum)."""
+    w = wl.small_points(4, m=40, n=52)
+    eta = 1e-2
+    f, g, it1, _ = po.sinkhorn(w.C, w.a, w.b, eta, max_iter=50000, tol=1e-11)
+    X = np.exp((f[:, None] + g[None, :] - w.C - eta) / eta)
+    cost1 = float(np.sum(w.C * X))
+    ref = po.pins(w.C, w.a, w.b, eta=eta, tol_marg=1e-11, K=1, T1=5000, T2=0)
+    out = _solve(pins.problem_from_workload(w), eta=eta, tol_marg=1e-11, K=1, T1=5000, T2=0)
+    assert out["outer_iters"] == 1 and out["newton_iters"] == 0
+    assert abs(out["sinkhorn_iters"] - ref["sinkhorn_iters"]) <= 10
+    assert out["marg_resid_l1"] <= 1e-10
+    assert abs(out["cost"] - cost1) / cost1 <= 1e-9
+
+
+def test_newton_without_eppa_converges_to_the_entropic_optimum():
+    """Newton without EPPA (K = 1): the sparse Newton phase after the warm-up
+    drives the residual to the tolerance and lands on the same entropic
+    optimum as Algorithm 1 at eps = eta."""
+    w = wl.small_points(4, m=40, n=52)
+    eta = 1e-2
+    f, g, _, _ = po.sinkhorn(w.C, w.a, w.b, eta, max_iter=50000, tol=1e-11)
+    cost1 = float(np.sum(w.C * np.exp((f[:, None] + g[None, :] - w.C - eta) / eta)))
+    ref = po.pins(w.C, w.a, w.b, eta=eta, tol_marg=1e-10, gamma=2.0, K=1, T2=300)
+    out = _solve(pins.problem_from_workload(w), eta=eta, tol_marg=1e-10, sparsify_gamma=2.0,
+                 K=1, T2=300)
+    assert out["outer_iters"] == 1 and out["sinkhorn_iters"] == ref["sinkhorn_iters"]
+    assert abs(out["newton_iters"] - ref["newton_iters"]) <= max(3, ref["newton_iters"] // 10)
+    assert out["marg_resid_l1"] <= 1e-10
+    assert abs(out["cost"] - cost1) / cost1 <= 1e-8
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_graph_warmup_matches_direct_launches(prec):
     """Unprofiled solves launch each block of Sinkhorn half-steps as one captured
