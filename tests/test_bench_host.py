@@ -1,0 +1,74 @@
+"""Host-side logic of bench.py that needs no GPU: the roofline object built from
+per-class timer totals, and the clock summary built from nvidia-smi samples."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_roofline_of_a_stored_cost_pass():
+    # row_lse dominates: 100 launches of 30 us over a 4096 x 4096 FP32 matrix
+    prof = {"row_lse": (3.0, 100), "col_lse": (2.0, 100), "cg": (1.0, 10)}
+    roof, dom = bench.roofline(prof, 4096, 4096, 4, cg_iters=500, nnz=8191,
+                               peaks={"hbm_gbs": 6800.0}, mixed=True)
+    assert dom == "row_lse"
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    want = 4096 * 4096 * 4 / 30e-6 / 1e9
+    assert roof["achieved"] == pytest.approx(want, rel=1e-12)
+    assert roof["frac"] == pytest.approx(want / 6800.0, rel=1e-12)
+    assert roof["peak_source"] == "measured"
+    assert roof["avg_launch_us"] == pytest.approx(30.0)
+
+
+def test_roofline_falls_back_without_measured_peaks():
+    roof, _ = bench.roofline({"trial": (1.0, 10)}, 64, 64, 8, 0, 0, peaks={}, mixed=False)
+    assert roof["peak"] == 6800.0 and roof["peak_source"] == "fallback"
+
+
+def test_roofline_of_the_mixed_cg_counts_double_float_operations():
+    m = n = 4096
+    nnz, launches, iters_total = 8191, 10, 540
+    prof = {"cg": (2.3, launches), "row_lse": (1.0, 100)}
+    roof, dom = bench.roofline(prof, m, n, 4, cg_iters=iters_total, nnz=nnz, peaks={},
+                               mixed=True)
+    assert dom == "cg" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    t = 2.3e-3 / launches
+    flops = (30.0 * nnz + 152.0 * (m + n)) * (iters_total / launches)
+    assert roof["achieved"] == pytest.approx(flops / t / 1e12, rel=1e-12)
+    assert roof["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"], rel=1e-12)
+    assert roof["iters_per_launch"] == pytest.approx(54.0)
+
+
+def test_roofline_of_the_fp64_cg_uses_the_fp64_rate():
+    roof, _ = bench.roofline({"cg": (1.0, 4)}, 100, 200, 8, cg_iters=40, nnz=299, peaks={},
+                             mixed=False)
+    flops = (4.0 * 299 + 14.0 * 300) * 10
+    assert roof["achieved"] == pytest.approx(flops / 250e-6 / 1e12, rel=1e-12)
+    assert roof["peak"] == bench.FP64_NOMINAL_TFLOPS
+
+
+def test_roofline_without_launches_is_absent():
+    roof, dom = bench.roofline({"cg": (0.0, 0)}, 8, 8, 4, 0, 0, peaks={}, mixed=True)
+    assert roof is None and dom == "cg"
+
+
+def test_clock_summary_takes_the_median_and_the_active_reasons():
+    cs = bench.ClockSampler()
+    cs.samples = [
+        ["2070", "2070", "900.1", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["1980", "2070", "1400.0", "Not Active", "Not Active", "Not Active", "Active"],
+        ["2070", "2070", "1200.5", "Not Active", "Not Active", "Not Active", "Not Active"],
+        ["[N/A]", "2070", "1200.5", "Not Active", "Not Active", "Not Active", "Not Active"],
+    ]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+
+
+def test_clock_summary_without_samples_says_so():
+    assert bench.ClockSampler().summary()["reasons"] == ["unsampled"]
