@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 def test_replica_rate_uses_the_slowest_rank():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of a threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
