@@ -219,6 +219,22 @@ def test_certificate_brackets_lp_optimum():
         np.testing.assert_allclose(R.sum(axis=0), b, atol=1e-14)
 
 
+def test_rounding_moves_the_plan_by_at_most_twice_its_marginal_error():
+    """Altschuler, Weed & Rigollet (2017), Lemma 7: the rounded plan is within
+    2 (||X 1 - a||_1 + ||X^T 1 - b||_1) of X in l1, and a plan that already has
+    the marginals is left as it is."""
+    rng = np.random.default_rng(16)
+    for m, n in [(4, 6), (9, 3), (12, 12)]:
+        a = rng.uniform(0.5, 1.5, size=m); a /= a.sum()
+        b = rng.uniform(0.5, 1.5, size=n); b /= b.sum()
+        X = rng.uniform(0.0, 2.0, size=(m, n)) / (m * n)
+        R = po.round_to_polytope(X, a, b)
+        err = np.abs(X.sum(axis=1) - a).sum() + np.abs(X.sum(axis=0) - b).sum()
+        assert np.abs(R - X).sum() <= 2.0 * err + 1e-15
+        P = np.outer(a, b)                               # feasible already
+        np.testing.assert_allclose(po.round_to_polytope(P, a, b), P, rtol=1e-14, atol=0)
+
+
 # --------------------------------------------------------------------------- #
 # End-to-end PINS against exact optima
 # --------------------------------------------------------------------------- #
