@@ -362,3 +362,19 @@ def test_table1_pins_accuracy_and_gap_factor_n50():
     err_sk = math.log10(abs(cost_sk - opt) / opt)
     assert err_pins <= case["pins_log10_rel_err"]
     assert err_sk - err_pins >= math.log10(case["gap_factor"])
+
+
+def test_table3_smaller_eta_needs_fewer_outer_iterations():
+    """Table 3: the outer iteration count falls steeply as eta shrinks (242, 60,
+    16, 4 at n = 400).  The seeded n = 50 draw of the same family, run to a
+    certified gap of 1e-4, shows the same trend between eta = 1e-2 and 1e-3."""
+    gold = json.load(open(os.path.join(GOLDEN, "table3_outer_iters.json")))
+    it = dict(zip(gold["eta"], gold["outer_iters"]))
+    p = wl.random_assignment(50, 0)
+    out = {}
+    for eta in (1e-2, 1e-3):
+        res = po.pins(p.C, p.a, p.b, eta=eta, K=250, tol_gap=1e-4)
+        assert res["rel_gap"] <= 1e-4
+        out[eta] = res["outer_iters"]
+    assert out[1e-2] >= 3 * out[1e-3]
+    assert it[0.01] >= 3 * it[0.001]                 # the printed trend itself
