@@ -72,8 +72,10 @@ typedef enum {
   /* m x n passes on the FP32 units: the Sinkhorn warm-up uses FP32 exp on a
    * double-float (compensated) exponent; the gradient, line-search, stopping and
    * certificate passes use a double-float table-driven exp (~1e-13 relative).
-   * Potentials, CG, dot products and stopping decisions stay FP64.  A dense
-   * FP64 cost is rounded to FP32 once. */
+   * The CG keeps its vectors and matrix-vector product in double-float (about
+   * 48 significand bits) with FP32 inner products, which steer only its step
+   * lengths.  Potentials, the outer update and the stopping decisions stay
+   * FP64.  A dense FP64 cost is rounded to FP32 once. */
   PINS_PREC_MIXED = 1
 } pins_precision;
 
@@ -160,7 +162,11 @@ void pins_destroy(pins_handle* h);
 const char* pins_last_error(pins_handle* h);
 
 /* Blocking solve of one problem (Algorithm 2) on the handle's stream.
- * Result fields are filled on PINS_OK and PINS_ERR_NOT_CONVERGED. */
+ * Result fields are filled on PINS_OK and PINS_ERR_NOT_CONVERGED.  With
+ * cfg.profile = 0, each block of sinkhorn_check_every warm-up iterations is
+ * captured once per outer iteration (thread-local capture mode on that stream)
+ * and launched as one CUDA graph; where capture is not possible the kernels
+ * are launched one by one.  Both give the same result. */
 pins_status pins_solve(pins_handle* h, const pins_problem* p, pins_result* r);
 
 /* Blocking solve of count independent problems.  Instances run concurrently on
