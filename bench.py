@@ -141,7 +141,7 @@ def measured_peaks():
 # kernel classes that stream the m x n matrix once per launch
 MN_CLASSES = ("row_lse", "col_lse", "marginals", "trial", "key_hist", "key_compact",
               "csr_write", "certificate")
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (no FP64 figure is measured by the driver)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 rate (the measured peaks file has no FP64 figure)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 units x clock, FMA = 2 flops
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
 # each class's kernel on this workload (mid-solve, caches flushed by ncu); the
