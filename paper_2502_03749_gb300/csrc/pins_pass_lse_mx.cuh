@@ -144,9 +144,12 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
       bulk_g2s(wbuf, p.cost.C32 + (size_t)i_first * n + j0, 4096u, &s_bar[warp][0]);
     }
     bool ok = true;
+    int fail_t = -1;                    // first row whose wait gave up
     for (int t = 0; t < T; ++t) {
       const int i = i_first + t * stride;
-      if (lane == 0 && t + 1 < T) {     // the buffer of row t - 1 was released by __syncwarp
+      // the buffer of row t - 1 was released by __syncwarp; no copy is issued
+      // once a wait of lane 0 has given up
+      if (lane == 0 && ok && t + 1 < T) {
         fence_proxy_async();
         mbar_expect_tx(&s_bar[warp][(t + 1) & 1], 4096u);
         bulk_g2s(wbuf + ((t + 1) & 1) * 1024, p.cost.C32 + (size_t)(i + stride) * n + j0, 4096u,
@@ -154,8 +157,10 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
       }
       // a wait that gives up (never expected) is recorded; later rows then skip
       // their waits so the pass still ends
-      if (ok && !mbar_wait_bounded(&s_bar[warp][t & 1], (unsigned int)((t >> 1) & 1), 1u << 22))
+      if (ok && !mbar_wait_bounded(&s_bar[warp][t & 1], (unsigned int)((t >> 1) & 1), 1u << 22)) {
         ok = false;
+        fail_t = t;
+      }
       const float* rowbuf = wbuf + (t & 1) * 1024;
       float M = -INFINITY, S = 0.f;
 #pragma unroll
@@ -179,6 +184,15 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
       if (lane == 0) store_f2(ws.rowpart0 + (size_t)x * m + i, M, S);
     }
     if (!ok && p.err) atomicOr(p.err, 16);
+    // before the warp leaves its buffers, lane 0 waits (again bounded) for the
+    // copies it may still have in flight: the one whose wait gave up and the
+    // prefetch issued just before that wait
+    if (lane == 0 && !ok) {
+      mbar_wait_bounded(&s_bar[warp][fail_t & 1], (unsigned int)((fail_t >> 1) & 1), 1u << 22);
+      if (fail_t + 1 < T)
+        mbar_wait_bounded(&s_bar[warp][(fail_t + 1) & 1], (unsigned int)(((fail_t + 1) >> 1) & 1),
+                          1u << 22);
+    }
   }
   for (int i = y * PINS_WARPS + warp; !full8 && i < m; i += GY * PINS_WARPS) {
     float M = -INFINITY, S = 0.f;
