@@ -150,7 +150,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # FP32 units x clock, FMA = 2
 NCU_TRAFFIC_BYTES = {
     "cg": None,              # k_pcg_dd changed after its capture (428 288 B then)
     "trial": 67849472,       # k_marg_mx<mixed,1>  (profiles/k_marg_mx_trial_gmm4096.md)
-    "row_lse": 67766016,     # k_row_lse_mx        (profiles/sinkhorn_lse_mx_gmm4096.md)
+    "row_lse": None,         # k_row_lse_mx changed after its capture (67 766 016 B then)
     "col_lse": None,         # k_col_lse_mx changed after its capture
     "key_compact": 67311360, # k_fast_collect      (profiles/sparsify_one_pass_gmm4096.md)
 }
