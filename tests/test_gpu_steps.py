@@ -50,6 +50,40 @@ def test_marginals(handles, prec, m, n):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_marginals_at_the_benchmark_size(prec):
+    """The benchmark's instance (4096 x 4096 GMM, eta = 1e-2) in the launch
+    configuration the solver uses at that size: every row and column sum of
+    the plan against the oracle on the same cost (FP32-rounded for the mixed
+    path), at potentials two Sinkhorn iterations into outer iteration 3."""
+    import torch
+    from paper_2502_03749_gb300 import workloads as wl
+    n = 4096
+    w = wl.gmm_instance(0, m=n, n=n, eta=1e-2)
+    C = w.C if prec == "fp64" else w.C.astype(np.float32).astype(np.float64)
+    eta, s = 1e-2, 3.0
+    F, G = np.zeros(n), np.zeros(n)
+    for _ in range(2):
+        F, _ = po.sinkhorn_row_step(C, w.a, F, G, eta, s)
+        G = po.sinkhorn_col_step(C, w.b, F, G, eta, s)
+    r = torch.zeros(n, dtype=torch.float64, device="cuda")
+    c = torch.zeros(n, dtype=torch.float64, device="cuda")
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    h = pins.Pins(prec=prec, eta=eta)
+    try:
+        prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, w.a, w.b)
+        st = pins.pins_step_marginals(h.h, prob.prob, s, dev(F), dev(G), r, c, out)
+        assert st == 0, h.error()
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+    _, _, r0, c0 = po.gradient(C, w.a, w.b, F, G, eta, s)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    np.testing.assert_allclose(r.cpu().numpy(), r0, rtol=tol)
+    np.testing.assert_allclose(c.cpu().numpy(), c0, rtol=tol)
+    assert out.cpu().numpy()[1] == pytest.approx(r0.sum(), rel=tol)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("m,n", SHAPES)
 def test_sinkhorn_half_steps(handles, prec, m, n):
     import torch
