@@ -39,7 +39,13 @@ Readings where the paper is silent (each is also listed in the design notes):
       iteration is taken instead.
   R8  Residual = ||X~ 1 - a||_1 + ||X~^T 1 - b||_1.
   R9  Outer stop: certified relative gap (UB - LB) / LB <= tol_gap, or K.
-      LB: c-transform of u = F/s - eta (LP weak duality).  UB: cost of the
+      LB: the larger of two LP weak-duality bounds, each the double c-transform
+      of a row potential: (i) u = F/s - eta, the subproblem's own dual, whose
+      bound trails OPT by O(eta/s); (ii) the support-tree dual: potentials that
+      satisfy u_i + v_j = C_ij exactly on a maximum-weight spanning forest of
+      the 2(m + n - 1) largest plan entries (complementary slackness on the
+      plan's support), which is an optimal LP dual once the plan has
+      concentrated on an optimal basis.  UB: cost of the
       Altschuler-Weed-Rigollet rounding of X~ onto the transport polytope.
 """
 from __future__ import annotations
@@ -287,6 +293,79 @@ def dual_lower_bound(C, a, b, F, eta, s):
     return float(a @ u2 + b @ v)
 
 
+def support_edges(C, F, G, eta, s, count):
+    """The `count` largest entries of X~ (key eta log X~ descending, ties -> lower
+    linear index i*n+j), as (keys, rows, cols) in that order."""
+    m, n = C.shape
+    key = key_matrix(C, F, G, eta, s).ravel()
+    lin = np.arange(m * n)
+    order = np.lexsort((lin, -key))[:count]
+    return key[order], order // n, order % n
+
+
+def support_tree_duals(C, F, G, eta, s, count=None):
+    """Support-tree dual (reading R9 (ii)).  Kruskal's maximum-weight spanning
+    forest over the `count` (default 2(m + n - 1)) largest plan entries, taken
+    in key order; nodes are the rows 0..m-1 and the columns m..m+n-1.  Each tree
+    is rooted at its lowest node, which keeps its entropic potential (rows
+    u_i = F_i/s - eta, columns v_j = G_j/s); every other node takes the value
+    that makes its tree edge tight, u_i + v_j = C_ij.  Returns (u, v, number of
+    trees)."""
+    m, n = C.shape
+    if count is None:
+        count = min(m * n, 2 * (m + n - 1))
+    _, rows, cols = support_edges(C, F, G, eta, s, count)
+    parent = list(range(m + n))
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    adj = [[] for _ in range(m + n)]
+    for i, j in zip(rows.tolist(), cols.tolist()):
+        ri, rj = find(i), find(m + j)
+        if ri != rj:
+            parent[max(ri, rj)] = min(ri, rj)
+            adj[i].append(m + j)
+            adj[m + j].append(i)
+    u = np.empty(m)
+    v = np.empty(n)
+    seen = [False] * (m + n)
+    trees = 0
+    for root in range(m + n):              # increasing node order: roots are lowest
+        if seen[root]:
+            continue
+        trees += 1
+        if root < m:
+            u[root] = F[root] / s - eta
+        else:
+            v[root - m] = G[root - m] / s
+        seen[root] = True
+        stack = [root]
+        while stack:
+            x = stack.pop()
+            for y in adj[x]:
+                if seen[y]:
+                    continue
+                seen[y] = True
+                if x < m:
+                    v[y - m] = C[x, y - m] - u[x]
+                else:
+                    u[y] = C[y, x - m] - v[x - m]
+                stack.append(y)
+    return u, v, trees
+
+
+def c_transform_bound(C, a, b, u):
+    """LP weak duality for any row potential u: v_j = min_i (C_ij - u_i), then
+    u'_i = min_j (C_ij - v_j) >= u_i; (u', v) is dual feasible, so
+    <a, u'> + <b, v> <= OPT."""
+    v = np.min(C - u[:, None], axis=0)
+    u2 = np.min(C - v[None, :], axis=1)
+    return float(a @ u2 + b @ v)
+
+
 def round_to_polytope(X, a, b):
     """Altschuler, Weed & Rigollet (2017), Algorithm 2: scale rows down to a,
     columns down to b, then add err_r err_c^T / ||err_r||_1."""
@@ -303,13 +382,17 @@ def round_to_polytope(X, a, b):
 
 
 def certificate(C, a, b, F, G, eta, s):
-    """Returns dict(cost=<C,X~>, lb, ub, rel_gap)."""
+    """Returns dict(cost=<C,X~>, lb, ub, rel_gap, lb_entropic, lb_tree)."""
     X = plan(C, F, G, eta, s)
     cost = float(np.sum(C * X))
     ub = float(np.sum(C * round_to_polytope(X, a, b)))
-    lb = dual_lower_bound(C, a, b, F, eta, s)
+    lb_e = dual_lower_bound(C, a, b, F, eta, s)
+    u_t, _, _ = support_tree_duals(C, F, G, eta, s)
+    lb_t = c_transform_bound(C, a, b, u_t)
+    lb = max(lb_e, lb_t)
     rel = (ub - lb) / lb if lb > 0.0 else (ub - lb) / max(abs(ub), 1e-300)
-    return {"cost": cost, "lb": lb, "ub": ub, "rel_gap": float(rel)}
+    return {"cost": cost, "lb": lb, "ub": ub, "rel_gap": float(rel),
+            "lb_entropic": lb_e, "lb_tree": lb_t}
 
 
 # --------------------------------------------------------------------------- #

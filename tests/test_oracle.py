@@ -219,6 +219,79 @@ def test_certificate_brackets_lp_optimum():
         np.testing.assert_allclose(R.sum(axis=0), b, atol=1e-14)
 
 
+def _nw_corner_1d(m, n, seed):
+    """A 1-D squared-cost instance with random weights and its optimum by the
+    north-west corner rule on sorted supports (Peyre & Cuturi, Remark 2.30)."""
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.uniform(0, 1, size=m))
+    y = np.sort(rng.uniform(0, 1, size=n))
+    a = rng.uniform(0.5, 1.5, size=m); a /= a.sum()
+    b = rng.uniform(0.5, 1.5, size=n); b /= b.sum()
+    C = (x[:, None] - y[None, :]) ** 2
+    C = C / C.max()
+    i = j = 0
+    ra, rb = a.copy(), b.copy()
+    opt = 0.0
+    while i < m and j < n:
+        t = min(ra[i], rb[j])
+        opt += t * C[i, j]
+        ra[i] -= t; rb[j] -= t
+        if ra[i] <= rb[j]:
+            i += 1
+        else:
+            j += 1
+    return C, a, b, opt
+
+
+def test_support_tree_is_the_maximum_spanning_forest():
+    """The support tree of the certificate is Kruskal's maximum-weight spanning
+    forest of the largest plan entries: the same edge set as SciPy's minimum
+    spanning tree on the negated keys (distinct keys, so the forest is unique), and
+    its potentials are tight on every forest edge, with each tree's lowest node
+    keeping its entropic potential."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    m, n = 9, 13
+    C, a, b, eta = _rand_problem(m, n, 41, eta=0.05)
+    rng = np.random.default_rng(42)
+    F, G = rng.normal(size=m) * 0.05, rng.normal(size=n) * 0.05
+    s = 2.0
+    count = 2 * (m + n - 1)
+    keys, rows, cols = po.support_edges(C, F, G, eta, s, count)
+    w = (keys.max() - keys) + 1.0                       # larger key -> lighter edge
+    g = coo_matrix((w, (rows, m + cols)), shape=(m + n, m + n)).tocsr()
+    mst = minimum_spanning_tree(g).tocoo()
+    want = {(int(i), int(j) - m) for i, j in zip(mst.row, mst.col)}
+    u, v, trees = po.support_tree_duals(C, F, G, eta, s, count)
+    tight = {(i, j) for i in range(m) for j in range(n)
+             if abs(u[i] + v[j] - C[i, j]) <= 1e-13}
+    assert want <= tight
+    assert len(want) == m + n - trees
+    # the roots (lowest node of each tree) keep the entropic potentials
+    assert u[0] == F[0] / s - eta
+
+
+def test_support_tree_bound_is_exact_on_a_concentrated_plan():
+    """Certificate LB (reading R9): on a 1-D instance with random weights (a
+    non-degenerate LP) whose plan has concentrated, the support-tree dual is an
+    optimal LP dual, so its bound equals the north-west-corner optimum to rounding,
+    while the entropic dual's bound still trails it by O(eta/s).  Both stay below
+    OPT for arbitrary potentials."""
+    C, a, b, opt = _nw_corner_1d(11, 14, 43)
+    res = po.pins(C, a, b, eta=1e-3, tol_marg=1e-12, K=6)
+    F, G, s = res["F"], res["G"], res["s"]
+    cert = po.certificate(C, a, b, F, G, 1e-3, s)
+    assert abs(cert["lb_tree"] - opt) <= 1e-13 * opt
+    assert opt - cert["lb_entropic"] > 1e-6 * opt
+    assert cert["lb"] == cert["lb_tree"]
+    rng = np.random.default_rng(44)
+    for _ in range(5):
+        Fr, Gr = rng.normal(size=11) * 0.2, rng.normal(size=14) * 0.2
+        c2 = po.certificate(C, a, b, Fr, Gr, 1e-2, 1.0)
+        assert c2["lb_tree"] <= opt * (1 + 1e-13)
+        assert c2["lb_entropic"] <= opt * (1 + 1e-13)
+
+
 def test_rounding_moves_the_plan_by_at_most_twice_its_marginal_error():
     """Altschuler, Weed & Rigollet (2017), Lemma 7: the rounded plan is within
     2 (||X 1 - a||_1 + ||X^T 1 - b||_1) of X in l1, and a plan that already has
