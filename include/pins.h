@@ -137,7 +137,9 @@ typedef struct {
                            against the LP optimum in Section 5) */
   double cost_ub;       /* cost of the plan rounded onto the transport polytope
                            (Altschuler-Weed-Rigollet), >= OPT */
-  double dual_lb;       /* c-transform dual bound, <= OPT */
+  double dual_lb;       /* LP dual bound, <= OPT: the larger of the c-transform
+                           bounds of the entropic dual and of the support-tree
+                           dual (see pins_step_certificate) */
   double rel_gap;       /* (cost_ub - dual_lb) / dual_lb */
   double marg_resid_l1; /* ||X~1 - a||_1 + ||X~^T 1 - b||_1 of the final plan */
   double s;             /* final scale: the plan is exp((F+G-s(C+eta))/eta) */
@@ -262,12 +264,21 @@ pins_status pins_step_objective_increase(pins_handle* h, const pins_problem* p,
                                          const double* dg, double alpha,
                                          double* out);
 
-/* Certificate of the stopping test: out4 (device, 4 doubles) = {<C, X~>,
- * UB = <C, round(X~)> (Altschuler-Weed-Rigollet rounding), LB = double
- * c-transform dual bound of u = F/s - eta, relative gap}. */
+/* Certificate of the stopping test (the outer stop of Algorithm 2; the bracket
+ * [LB, UB] bounds the relative error to the LP optimum that Section 5 reports):
+ * out6 (device, 6 doubles) = {<C, X~>, UB = <C, round(X~)>
+ * (Altschuler-Weed-Rigollet rounding), LB, relative gap (UB - LB) / LB,
+ * LB_entropic, LB_tree}.  LB = max(LB_entropic, LB_tree), each the double
+ * c-transform bound <a, u'> + <b, v> of a row potential: LB_entropic from
+ * u = F/s - eta; LB_tree from the support-tree dual, i.e. potentials tight
+ * (u_i + v_j = C_ij) on the maximum-weight spanning forest of the
+ * 2(m + n - 1) largest entries of X~ (ranked by F_i + G_j - s (C_ij + eta),
+ * ties to the lower row-major index; each tree's lowest node, rows first,
+ * keeps its entropic potential).  Both are valid LP lower bounds for any F, G;
+ * LB_tree reaches OPT once the plan has concentrated on an optimal basis. */
 pins_status pins_step_certificate(pins_handle* h, const pins_problem* p,
                                   double s, const double* F, const double* G,
-                                  double* out4);
+                                  double* out6);
 
 /* ------------------------------------------------------------------------- */
 /* Allocation-free marginal pass.  The paper has no counterpart: this entry   */

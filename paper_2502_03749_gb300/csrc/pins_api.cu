@@ -442,8 +442,8 @@ extern "C" pins_status pins_step_objective_increase(pins_handle* h, const pins_p
 }
 
 extern "C" pins_status pins_step_certificate(pins_handle* h, const pins_problem* p, double s,
-                                             const double* F, const double* G, double* out4) {
+                                             const double* F, const double* G, double* out6) {
   PINS_STEP_GUARD(h, p);
-  if (!F || !G || !out4) return PINS_ERR_INVALID_ARG;
-  return step_result(h, h->solver->step_certificate(h->cfg, *p, s, F, G, out4));
+  if (!F || !G || !out6) return PINS_ERR_INVALID_ARG;
+  return step_result(h, h->solver->step_certificate(h->cfg, *p, s, F, G, out6));
 }

@@ -194,6 +194,18 @@ __device__ __forceinline__ float expm1_minus_x(float y) {
   return __fsub_rn(__fsub_rn(expf(y), 1.0f), y);
 }
 
+// Line-search objective term X~ (expm1(t) - t) >= 0 of one entry (mixed
+// policy), from z0 = log X~ (FP32), t and e1 = X~ e^t (the trial entry, already
+// formed in double-float).  For |t| < 1/2 the series form is free of
+// cancellation; otherwise the term is e1 - X~ (1 + t), which loses at most a
+// few bits there and stays finite when X~ underflows FP32 (z0 < -87) while e^t
+// alone would overflow.
+__device__ __forceinline__ float trial_term(float z0, float t, float e1) {
+  const float x0 = (z0 > -87.0f) ? exp2f(__fmul_rn(z0, 1.4426950408889634f)) : 0.0f;
+  if (fabsf(t) < 0.5f) return __fmul_rn(x0, expm1_minus_x(t));
+  return fmaxf(0.0f, __fsub_rn(e1, __fmul_rn(x0, __fadd_rn(1.0f, t))));
+}
+
 // expm1 of a double-float argument with relative accuracy ~2^-44 for small |t|.
 __device__ __forceinline__ dd dd_expm1(float th, float tl, const float2* __restrict__ T) {
   dd r;
@@ -443,8 +455,10 @@ struct MergeWS {
   double* rowpart2;        // gx * m
   double* rowpart3;        // gx * m
   double* rowpart4;        // gx * m
+  double* rowpart5;        // gx * m (certificate only)
   double* colpart0;        // gy * n
   double* colpart1;        // gy * n
+  double* colpart2;        // gy * n (certificate only)
   double* scal_row;        // gy * 8 per-row-block scalar partials
   double* scal_col;        // gx * 8 per-strip scalar partials
 };

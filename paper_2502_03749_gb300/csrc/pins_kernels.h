@@ -12,6 +12,7 @@ namespace pins {
 struct SparsifyState;
 struct TrialArgs;
 struct CertArgs;
+struct TreeWS;
 
 // One-pass selection used between Newton steps of one outer iteration on the
 // mixed path: every entry whose key is at least tau_guess (the previous step's
@@ -57,6 +58,9 @@ struct PassSet {
   // one-pass candidate collection (mixed policy only; nullptr otherwise)
   void (*fast_collect)(const PassArgs&, float tau_guess, FastSelState*, float* ckey,
                        unsigned long long* cij, int blocks, cudaStream_t);
+  // support-tree dual of the certificate from a CSR of the largest entries
+  void (*tree_duals)(const PassArgs&, const int* indptr, const int* indices, int ne,
+                     const TreeWS&, double* uT, int* err, cudaStream_t);
 };
 
 const PassSet* passes_f64(int kind);
@@ -119,9 +123,12 @@ void launch_cert_pre(const double* a, const double* r, const double* F, int m, d
                      double eta, double* xs, double* u, cudaStream_t st);
 void launch_cert_mid(const double* b, const double* c1, int n, double* ys, double* ec,
                      cudaStream_t st);
+// out4 = {cost, UB, LB, gap} with LB the larger of the two dual bounds; lb2 (may be
+// NULL) = {entropic-dual bound, support-tree bound}
 void launch_cert_final(const double* a, const double* b, const double* rr, const double* cr,
                        const double* cp, const double* tc, const double* u2, const double* v,
-                       int m, int n, double* out4, cudaStream_t st);
+                       const double* u2T, const double* vT, int m, int n, double* out4,
+                       double* lb2, cudaStream_t st);
 void launch_d2f(const double* x, float* y, size_t N, cudaStream_t st);
 void launch_f2d(const float* x, double* y, size_t N, cudaStream_t st);
 

@@ -124,9 +124,13 @@ template <int K> struct Launch {
     if constexpr (P::MIXED)
       k_fast_collect<P><<<blocks, PINS_TPB, 0, st>>>(p, tau_guess, fs, ckey, cij);
   }
+  static void tree_duals(const PassArgs& p, const int* indptr, const int* indices, int ne,
+                         const TreeWS& tw, double* uT, int* err, cudaStream_t st) {
+    k_tree_duals<P><<<1, PINS_TREE_TPB, 0, st>>>(p, indptr, indices, ne, tw, uT, err);
+  }
   static const PassSet* get() {
     static const PassSet ps = {P::MIXED, row_lse, col_lse, marg, cert, key_hist, key_compact,
-                               key_write, P::MIXED ? fast_collect : nullptr};
+                               key_write, P::MIXED ? fast_collect : nullptr, tree_duals};
     return &ps;
   }
 };

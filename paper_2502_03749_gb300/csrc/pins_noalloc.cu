@@ -131,6 +131,9 @@ extern "C" pins_status pins_marginals_noalloc(const pins_problem* p, double eta,
       kind = COST_GRID; break;
     default: return PINS_ERR_INVALID_ARG;
   }
+  // an error already pending from unrelated work is left for its owner: only
+  // an error that appears during this call is reported (and cleared)
+  const cudaError_t pending = cudaPeekAtLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return PINS_ERR_CUDA; }
   unsigned char* base = nullptr;
@@ -191,5 +194,9 @@ extern "C" pins_status pins_marginals_noalloc(const pins_problem* p, double eta,
   double* out4 = reinterpret_cast<double*>(base + L.out4);
   ps->marg(pa, g, ws, nullptr, r, c, out4, st);
   k_noalloc_out3<<<1, 1, 0, st>>>(out4, eta, out3);
-  return cudaGetLastError() == cudaSuccess ? PINS_OK : PINS_ERR_CUDA;
+  if (pending == cudaSuccess && cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return PINS_ERR_CUDA;
+  }
+  return PINS_OK;
 }

@@ -1,9 +1,10 @@
 // Certificate passes of the outer stopping test (reading R9).
 //   Column pass: c1_j = sum_i X~_ij xs_i  (xs_i = min(a_i / r_i, 1)),
-//                v_j  = min_i (C_ij - u_i) (u_i = F_i / s - eta).
+//                v_j  = min_i (C_ij - u_i) (u_i = F_i / s - eta),
+//                vT_j = min_i (C_ij - uT_i) (uT: the support-tree dual).
 //   Row pass:    rr_i = sum_j X~_ij xs_i ys_j, cr_i = sum_j C_ij X~_ij xs_i ys_j,
 //                cp_i = sum_j C_ij X~_ij, tc_i = sum_j C_ij ec_j,
-//                u2_i = min_j (C_ij - v_j).
+//                u2_i = min_j (C_ij - v_j), u2T_i = min_j (C_ij - vT_j).
 // C_ij: the FP64 policy evaluates it in FP64; the mixed policy uses cscale * c32
 // in FP64 (the FP32 raw cost is the definition of C there).  The entries are
 // summed in FP64 (this pass runs once per certificate, not per step).
@@ -14,6 +15,7 @@ namespace pins {
 struct CertArgs {
   const double* xs; const double* ys; const double* u; const double* v; const double* ec;
   double* c1; double* vout; double* rr; double* cr; double* cp; double* tc; double* u2;
+  const double* uT; double* vTout; const double* vT; double* u2T;
 };
 
 template <class P>
@@ -47,15 +49,15 @@ k_cert(PassArgs p, TileGeom g, MergeWS ws, CertArgs ca) {
   }
   for (int ct = blockIdx.x; ct < g.nct; ct += g.gx) {
     const bool first = (ct == (int)blockIdx.x);
-    double cs[PINS_CPL], cmin[PINS_CPL];
+    double cs[PINS_CPL], cmin[PINS_CPL], cmin2[PINS_CPL];
 #pragma unroll
-    for (int q = 0; q < PINS_CPL; ++q) { cs[q] = 0.0; cmin[q] = INFINITY; }
+    for (int q = 0; q < PINS_CPL; ++q) { cs[q] = 0.0; cmin[q] = INFINITY; cmin2[q] = INFINITY; }
     for (int rt = blockIdx.y; rt < g.nrt; rt += g.gy) {
       for (int t = 0; t < PINS_RPT; ++t) {
         const int i = rt * PINS_TR + warp + PINS_WARPS * t;
         if (i >= m) break;
         const double x_i = ca.xs[i];
-        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, rmin = INFINITY;
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0, rmin = INFINITY, rmin2 = INFINITY;
 #pragma unroll
         for (int q = 0; q < PINS_CPL; ++q) {
           const int j = ct * PINS_TC + lane + 32 * q;
@@ -65,21 +67,25 @@ k_cert(PassArgs p, TileGeom g, MergeWS ws, CertArgs ca) {
           if constexpr (COLPASS) {
             cs[q] += e * x_i;
             cmin[q] = fmin(cmin[q], C - ca.u[i]);
+            cmin2[q] = fmin(cmin2[q], C - ca.uT[i]);
           } else {
             const double ey = e * x_i * ca.ys[j];
             r0 += ey; r1 += C * ey; r2 += C * e; r3 += C * ca.ec[j];
             rmin = fmin(rmin, C - ca.v[j]);
+            rmin2 = fmin(rmin2, C - ca.vT[j]);
           }
         }
         if constexpr (!COLPASS) {
           r0 = warp_sum(r0); r1 = warp_sum(r1); r2 = warp_sum(r2); r3 = warp_sum(r3);
           rmin = warp_mind(rmin);
+          rmin2 = warp_mind(rmin2);
           if (lane == 0) {
             const size_t k = (size_t)blockIdx.x * m + i;
             if (first) { ws.rowpart0[k] = r0; ws.rowpart1[k] = r1; ws.rowpart2[k] = r2;
-                         ws.rowpart3[k] = r3; ws.rowpart4[k] = rmin; }
+                         ws.rowpart3[k] = r3; ws.rowpart4[k] = rmin; ws.rowpart5[k] = rmin2; }
             else { ws.rowpart0[k] += r0; ws.rowpart1[k] += r1; ws.rowpart2[k] += r2;
-                   ws.rowpart3[k] += r3; ws.rowpart4[k] = fmin(ws.rowpart4[k], rmin); }
+                   ws.rowpart3[k] += r3; ws.rowpart4[k] = fmin(ws.rowpart4[k], rmin);
+                   ws.rowpart5[k] = fmin(ws.rowpart5[k], rmin2); }
           }
         }
       }
@@ -100,6 +106,16 @@ k_cert(PassArgs p, TileGeom g, MergeWS ws, CertArgs ca) {
           ws.colpart0[(size_t)blockIdx.y * n + j] = S;
           ws.colpart1[(size_t)blockIdx.y * n + j] = Mn;
         }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < PINS_CPL; ++q) stg[0][warp * PINS_TC + lane + 32 * q] = cmin2[q];
+      __syncthreads();
+      for (int c = threadIdx.x; c < PINS_TC; c += PINS_TPB) {
+        double Mn = INFINITY;
+        for (int w = 0; w < PINS_WARPS; ++w) Mn = fmin(Mn, stg[0][w * PINS_TC + c]);
+        const int j = ct * PINS_TC + c;
+        if (j < n) ws.colpart2[(size_t)blockIdx.y * n + j] = Mn;
       }
       __syncthreads();
     }
@@ -123,23 +139,34 @@ k_cert(PassArgs p, TileGeom g, MergeWS ws, CertArgs ca) {
           __syncthreads();
         }
         if ((int)threadIdx.x < nc) { ca.c1[j0 + threadIdx.x] = S; ca.vout[j0 + threadIdx.x] = Mn; }
+        double Mn2 = INFINITY;
+        for (int y0 = 0; y0 < g.gy; y0 += 16) {
+          const int cnt = min(16, g.gy - y0);
+          stage8(ws.colpart2 + (size_t)y0 * n + j0, n, cnt, PINS_TC, nc, stg[0]);
+          __syncthreads();
+          if ((int)threadIdx.x < nc)
+            for (int s = 0; s < cnt; ++s) Mn2 = fmin(Mn2, stg[0][s * PINS_TC + threadIdx.x]);
+          __syncthreads();
+        }
+        if ((int)threadIdx.x < nc) ca.vTout[j0 + threadIdx.x] = Mn2;
       }
     }
   } else {
     if (arrive_last(ws.cnt_row + blockIdx.y, g.gx)) {
-      double* parts[5] = {ws.rowpart0, ws.rowpart1, ws.rowpart2, ws.rowpart3, ws.rowpart4};
-      double* outs[5] = {ca.rr, ca.cr, ca.cp, ca.tc, ca.u2};
+      double* parts[6] = {ws.rowpart0, ws.rowpart1, ws.rowpart2, ws.rowpart3, ws.rowpart4,
+                          ws.rowpart5};
+      double* outs[6] = {ca.rr, ca.cr, ca.cp, ca.tc, ca.u2, ca.u2T};
       for (int rt = blockIdx.y; rt < g.nrt; rt += g.gy) {
         const int i0 = rt * PINS_TR;
         const int nr = min(PINS_TR, m - i0);
-        for (int a = 0; a < 5; ++a) {
+        for (int a = 0; a < 6; ++a) {
           stage8(parts[a] + i0, m, g.gx, PINS_TR, nr, stg[0]);
           __syncthreads();
           if ((int)threadIdx.x < nr) {
-            double acc = (a == 4) ? INFINITY : 0.0;
+            double acc = (a >= 4) ? INFINITY : 0.0;
             for (int x = 0; x < g.gx; ++x) {
               const double v = stg[0][x * PINS_TR + threadIdx.x];
-              acc = (a == 4) ? fmin(acc, v) : acc + v;
+              acc = (a >= 4) ? fmin(acc, v) : acc + v;
             }
             outs[a][i0 + threadIdx.x] = acc;
           }

@@ -156,10 +156,15 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
                  &s_bar[warp][(t + 1) & 1]);
       }
       // a wait that gives up (never expected) is recorded; later rows then skip
-      // their waits so the pass still ends
-      if (ok && !mbar_wait_bounded(&s_bar[warp][t & 1], (unsigned int)((t >> 1) & 1), 1u << 22)) {
-        ok = false;
-        fail_t = t;
+      // their waits so the pass still ends.  The outcome is made warp-uniform:
+      // if any lane gave up, every lane stops waiting and lane 0 issues no
+      // further copy, so the drain below covers every lane's failure.
+      if (ok) {
+        const bool waited = mbar_wait_bounded(&s_bar[warp][t & 1], (unsigned int)((t >> 1) & 1), 1u << 22);
+        if (!__all_sync(0xffffffffu, waited)) {
+          ok = false;
+          fail_t = t;
+        }
       }
       const float* rowbuf = wbuf + (t & 1) * 1024;
       float M = -INFINITY, S = 0.f;

@@ -115,9 +115,11 @@ k_marg(PassArgs p, TileGeom g, MergeWS ws, TrialArgs tr, double* r_out, double* 
               zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
               // X~ below e^-87 at both points: no term of any sum changes
               if (!(z0 > -87.0f) && !(zh > -87.0f)) continue;
-              // objective term X~ (expm1(t) - t) >= 0: FP32 suffices (no cancellation)
-              const float ef = exp2f(z0 * 1.4426950408889634f);
-              dfs = __fmaf_rn(ef, expm1_minus_x(tf), dfs);
+              const dd e = dd_exp(zh, zl, s_tab);
+              dd_acc(racc, e.hi, e.lo);
+              dd_acc(cdd[q], e.hi, e.lo);
+              dfs = __fadd_rn(dfs, trial_term(z0, tf, e.hi));
+              continue;
             } else {
               zmaxf = fmaxf(zmaxf, __fadd_rn(zh, zl));
               if (!(zh > -87.0f)) continue;   // dd_exp gives 0: nothing to add

@@ -131,10 +131,7 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
         dd cc; cc.hi = o.x; cc.lo = o.y;
         dd_acc(cc, e.hi, e.lo);
         wacc[col] = make_float2(cc.hi, cc.lo);
-        if constexpr (TRIAL) {
-          // objective term X~ (expm1(t) - t) >= 0 in FP32 (no cancellation)
-          if (z0 > -87.0f) dfs = __fmaf_rn(exp2f(z0 * 1.4426950408889634f), expm1_minus_x(tf), dfs);
-        }
+        if constexpr (TRIAL) dfs = __fadd_rn(dfs, trial_term(z0, tf, e.hi));
       }
       __syncwarp();
     }

@@ -125,3 +125,4 @@ __device__ __forceinline__ float2 as_f2(double v) { return *reinterpret_cast<flo
 #include "pins_pass_marg.cuh"
 #include "pins_pass_marg_mx.cuh"
 #include "pins_pass_cert.cuh"
+#include "pins_tree.cuh"

@@ -71,14 +71,22 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.u2 = cv.take<double>(m);
   w.ys = cv.take<double>(n); w.ec = cv.take<double>(n); w.c1 = cv.take<double>(n);
   w.v = cv.take<double>(n);
+  w.uT = cv.take<double>(m); w.u2T = cv.take<double>(m); w.vT = cv.take<double>(n);
+  w.tw.erow = cv.take<int>(kcap); w.tw.okey = cv.take<unsigned long long>(kcap);
+  w.tw.eflag = cv.take<int>(kcap);
+  w.tw.comp = cv.take<int>(N); w.tw.bkey = cv.take<unsigned long long>(N);
+  w.tw.be = cv.take<int>(N); w.tw.lvl = cv.take<int>(N); w.tw.minid = cv.take<int>(N);
+  w.tw.pot = cv.take<double>(N);
   w.Add = cv.take<float2>(m); w.Bdd = cv.take<float2>(n);
   w.mws.rowpart0 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart1 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart2 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart3 = cv.take<double>((size_t)g.gx * m);
   w.mws.rowpart4 = cv.take<double>((size_t)g.gx * m);
+  w.mws.rowpart5 = cv.take<double>((size_t)g.gx * m);
   w.mws.colpart0 = cv.take<double>((size_t)g.gy * n);
   w.mws.colpart1 = cv.take<double>((size_t)g.gy * n);
+  w.mws.colpart2 = cv.take<double>((size_t)g.gy * n);
   w.mws.scal_row = cv.take<double>(8 * PINS_GY_MAX);
   w.mws.scal_col = cv.take<double>(4 * PINS_GX_MAX * PINS_GY_MAX + PINS_GX_MAX);
   w.mws.cnt_row = cv.take<unsigned int>(PINS_ROW_GROUPS);
@@ -310,9 +318,12 @@ pins_status Solver::prepare(const pins_config& cfg, const pins_problem& p, bool 
   ps_ = mixed_ ? passes_mixed(kind) : passes_f64(kind);
   m_ = p.m; n_ = p.n; eta_ = cfg.eta;
   geom_ = make_geom(m_, n_);
+  // the kept entries of a Newton step, and the certificate's support: the
+  // 2(m + n - 1) largest entries (reading R9 (ii))
+  const long long ksup = 2LL * (m_ + n_ - 1);
   int kcap = need_kcap ? (int)std::min<long long>((long long)m_ * n_,
-                                                   std::max(1LL, (long long)llround(cfg.sparsify_gamma * (m_ + n_ - 1))))
-                       : 1;
+                                                   std::max({1LL, ksup, (long long)llround(cfg.sparsify_gamma * (m_ + n_ - 1))}))
+                       : (int)std::min<long long>((long long)m_ * n_, ksup);
   int t1cap = std::max(cfg.T1, 1);
   pins_status s = ensure(m_, n_, kcap, t1cap, p.kind, mixed_, !p.on_device, p.d);
   if (s != PINS_OK) return s;
@@ -454,7 +465,7 @@ void Solver::marg(double s, bool trial, double alpha) {
   ++launches_;
 }
 
-pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out) {
+pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out, bool csc) {
   // window: 64 nats of z below the largest key (X~ ratio e^-64), widened or
   // refined by the select kernel until the threshold bin fits the candidates
   SparsifyState st{};
@@ -508,10 +519,13 @@ pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out) {
   launch_scan(ws_.sw.rowcnt, ws_.sw.indptr, m_, stream_);
   ps_->key_write(pa, ws_.st, ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, blocks, stream_);
   prof_end();
-  prof_begin(PC_CSC);
-  build_csc_from_csr(ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, m_, n_, keep, ws_.sw, stream_);
-  prof_end();
-  launches_ += 6;
+  launches_ += 2;
+  if (csc) {
+    prof_begin(PC_CSC);
+    build_csc_from_csr(ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, m_, n_, keep, ws_.sw, stream_);
+    prof_end();
+    launches_ += 4;
+  }
   *nnz_out = keep;
   return check("csr");
 }
@@ -532,18 +546,35 @@ void Solver::sparsify_fast(double s, int keep, float tau_guess) {
   launches_ += 6;
 }
 
-pins_status Solver::certificate(double s) {
-  launch_cert_pre(a_, ws_.r, ws_.F, m_, s, eta_, ws_.xs, ws_.u, stream_);
+pins_status Solver::certificate(double s, double zmax) {
+  // support-tree dual (reading R9 (ii)): the 2(m + n - 1) largest entries, a
+  // maximum-weight spanning forest, potentials tight on its edges.  Where the
+  // selection cannot resolve its threshold (more tied keys than the candidate
+  // buffer), the tree dual is the entropic one and the bound is unchanged.
+  const int ksup = (int)std::min<long long>((long long)m_ * n_, 2LL * (m_ + n_ - 1));
+  int nnz = 0;
   prep(s);
+  const std::string err_keep = err_;
+  const bool have_tree = ksup <= ws_.kcap && sparsify(s, ksup, zmax, &nnz, false) == PINS_OK;
+  launch_cert_pre(a_, ws_.r, ws_.F, m_, s, eta_, ws_.xs, ws_.u, stream_);
+  ++launches_;
   PassArgs pa = args(s, ws_.F, ws_.G);
-  CertArgs ca{ws_.xs, ws_.ys, ws_.u, ws_.v, ws_.ec, ws_.c1, ws_.v, ws_.rr, ws_.cr, ws_.cp,
-              ws_.tc, ws_.u2};
   prof_begin(PC_CERT);
+  if (have_tree) {
+    ps_->tree_duals(pa, ws_.sw.indptr, ws_.sw.indices, ksup, ws_.tw, ws_.uT,
+                    reinterpret_cast<int*>(ws_.scal + SC_FLAG), stream_);
+  } else {
+    err_ = err_keep;
+    cudaGetLastError();
+    cudaMemcpyAsync(ws_.uT, ws_.u, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
+  }
+  CertArgs ca{ws_.xs, ws_.ys, ws_.u, ws_.v, ws_.ec, ws_.c1, ws_.v, ws_.rr, ws_.cr, ws_.cp,
+              ws_.tc, ws_.u2, ws_.uT, ws_.vT, ws_.vT, ws_.u2T};
   ps_->cert(pa, geom_, ws_.mws, ca, true, stream_);
   launch_cert_mid(b_, ws_.c1, n_, ws_.ys, ws_.ec, stream_);
   ps_->cert(pa, geom_, ws_.mws, ca, false, stream_);
-  launch_cert_final(a_, b_, ws_.rr, ws_.cr, ws_.cp, ws_.tc, ws_.u2, ws_.v, m_, n_,
-                    ws_.scal + SC_CERT, stream_);
+  launch_cert_final(a_, b_, ws_.rr, ws_.cr, ws_.cp, ws_.tc, ws_.u2, ws_.v, ws_.u2T, ws_.vT, m_, n_,
+                    ws_.scal + SC_CERT, ws_.scal + SC_CERT2, stream_);
   prof_end();
   launches_ += 5;
   return check("certificate");
@@ -699,7 +730,8 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
           std::memcpy(&flag, h_scal_ + SC_FLAG, sizeof(int));
           if (flag) {
             err_ = std::string((flag & 16) ? "a bulk-copy wait gave up in a Sinkhorn pass"
-                                           : "cg: an index outside the cluster's slices was skipped") +
+                               : (flag & 32) ? "certificate: the spanning-forest build did not settle"
+                                             : "cg: an index outside the cluster's slices was skipped") +
                    " (flag " + std::to_string(flag) + ")";
             r.status = PINS_ERR_CUDA;
             return PINS_ERR_CUDA;
@@ -743,7 +775,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
     outer = k + 1;
     // ---- outer stop (reading R9) ----
     if (cfg.tol_gap > 0.0 && (outer % gap_every == 0 || outer == cfg.K)) {
-      if ((stt = certificate(s)) != PINS_OK) { r.status = stt; return stt; }
+      if ((stt = certificate(s, zmax)) != PINS_OK) { r.status = stt; return stt; }
       cudaMemcpyAsync(cert, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
       if ((stt = sync("certificate")) != PINS_OK) { r.status = stt; return stt; }
       cert_current = true;
@@ -756,7 +788,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
   }
   const double s_final = (double)outer;
   if (!cert_current) {
-    if ((stt = certificate(s_final)) != PINS_OK) { r.status = stt; return stt; }
+    if ((stt = certificate(s_final, zmax)) != PINS_OK) { r.status = stt; return stt; }
     cudaMemcpyAsync(cert, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToHost, stream_);
   }
   if (r.F_out) cudaMemcpyAsync(r.F_out, ws_.F, sizeof(double) * m, cudaMemcpyDeviceToHost, stream_);
@@ -926,15 +958,20 @@ pins_status Solver::step_objective_increase(const pins_config& cfg, const pins_p
 }
 
 pins_status Solver::step_certificate(const pins_config& cfg, const pins_problem& p, double s,
-                                     const double* F, const double* G, double* out4) {
+                                     const double* F, const double* G, double* out6) {
   pins_status st = prepare(cfg, p, false);
   if (st != PINS_OK) return st;
   cudaMemcpyAsync(ws_.F, F, sizeof(double) * m_, cudaMemcpyDeviceToDevice, stream_);
   cudaMemcpyAsync(ws_.G, G, sizeof(double) * n_, cudaMemcpyDeviceToDevice, stream_);
   prep(s);
   marg(s, false);
-  if ((st = certificate(s)) != PINS_OK) return st;
-  cudaMemcpyAsync(out4, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
+                  cudaMemcpyDeviceToHost, stream_);
+  if ((st = sync("step_certificate marg")) != PINS_OK) return st;
+  if ((st = certificate(s, h_scal_[SC_MARG + 2])) != PINS_OK) return st;
+  cudaMemcpyAsync(out6, ws_.scal + SC_CERT, 4 * sizeof(double), cudaMemcpyDeviceToDevice, stream_);
+  cudaMemcpyAsync(out6 + 4, ws_.scal + SC_CERT2, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                  stream_);
   return sync("step_certificate");
 }
 

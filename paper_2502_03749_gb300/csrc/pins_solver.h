@@ -18,6 +18,8 @@ struct Workspace {
   double *F, *G, *Phi, *Psi, *A64, *B64, *r, *c, *rt, *ct, *Pt64, *Qt64;
   double *grad, *dir, *cg_res, *cg_p, *cg_q, *ab;
   double *xs, *u, *rr, *cr, *cp, *tc, *u2, *ys, *ec, *c1, *v;
+  double *uT, *vT, *u2T;   // support-tree dual of the certificate
+  TreeWS tw;
   float2 *Add, *Bdd;
   MergeWS mws;
   SparsifyState* st;
@@ -42,7 +44,7 @@ class Solver {
   // scalar slots in Workspace::scal (doubles)
   // (SC_STATE: 12 doubles of pinned host memory receive the SparsifyState)
   enum { SC_MARG = 0, SC_TRIAL = 4, SC_DOTS = 8, SC_CERT = 12, SC_CG = 16, SC_STATE = 18,
-         SC_FLAG = 30, SC_FAST = 32, SC_ROWRES = 40 };
+         SC_FLAG = 30, SC_FAST = 32, SC_CERT2 = 36, SC_ROWRES = 40 };
 
   Solver(int device, int sms, const float2* exp_table);
   ~Solver();
@@ -74,7 +76,7 @@ class Solver {
                                       const double* F, const double* G, const double* df,
                                       const double* dg, double alpha, double* out);
   pins_status step_certificate(const pins_config& cfg, const pins_problem& p, double s,
-                               const double* F, const double* G, double* out4);
+                               const double* F, const double* G, double* out6);
 
   const std::string& error() const { return err_; }
   // the CG of one Newton step (double-float cluster kernel on the mixed path when
@@ -113,11 +115,13 @@ class Solver {
   void prep(double s);
   void sinkhorn_iter(double s, int t);
   void marg(double s, bool trial, double alpha = 0.0);
-  pins_status sparsify(double s, int keep, double zmax, int* nnz_out);
+  pins_status sparsify(double s, int keep, double zmax, int* nnz_out, bool csc = true);
   // one-pass selection for the later Newton steps of an outer iteration (mixed);
   // launches only, the outcome is read at the next line-search sync
   void sparsify_fast(double s, int keep, float tau_guess);
-  pins_status certificate(double s);
+  // certificate at (F, G, s); zmax = max_ij z at that point (window of the
+  // support selection of the tree dual)
+  pins_status certificate(double s, double zmax);
   PassArgs args(double s, const double* F, const double* G);
 
   int device_, sms_;

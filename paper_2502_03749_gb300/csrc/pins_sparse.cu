@@ -521,30 +521,36 @@ __global__ void k_cert_mid(const double* b, const double* c1, int n, double* ys,
     ec[j] = b[j] - y * c1[j];
   }
 }
-// final scalars: cost, UB, LB, gap (one CTA, fixed order)
+// final scalars: cost, UB, LB, gap (one CTA, fixed order).  LB is the larger of
+// the two c-transform bounds: <a, u2> + <b, v> (entropic dual) and
+// <a, u2T> + <b, vT> (support-tree dual).
 __global__ void __launch_bounds__(256) k_cert_final(const double* a, const double* b,
                                                     const double* rr, const double* cr,
                                                     const double* cp, const double* tc,
                                                     const double* u2, const double* v,
-                                                    int m, int n, double* out4) {
+                                                    const double* u2T, const double* vT,
+                                                    int m, int n, double* out4, double* lb2) {
   __shared__ double sh[32];
-  double s_cost = 0, s_cr = 0, s_er = 0, s_ert = 0, s_lb = 0;
+  double s_cost = 0, s_cr = 0, s_er = 0, s_ert = 0, s_lb = 0, s_lbt = 0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     double er = a[i] - rr[i];
     s_cost += cp[i]; s_cr += cr[i]; s_er += fabs(er); s_ert += er * tc[i];
     s_lb += a[i] * u2[i];
+    s_lbt += a[i] * u2T[i];
   }
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s_lb += b[j] * v[j];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) { s_lb += b[j] * v[j]; s_lbt += b[j] * vT[j]; }
   double t0 = cg_block_sum(s_cost, sh); __syncthreads();
   double t1 = cg_block_sum(s_cr, sh); __syncthreads();
   double t2 = cg_block_sum(s_er, sh); __syncthreads();
   double t3 = cg_block_sum(s_ert, sh); __syncthreads();
-  double t4 = cg_block_sum(s_lb, sh);
+  double t4 = cg_block_sum(s_lb, sh); __syncthreads();
+  double t5 = cg_block_sum(s_lbt, sh);
   if (threadIdx.x == 0) {
     double ub = t1 + (t2 > 0.0 ? t3 / t2 : 0.0);
-    double lb = t4;
+    double lb = fmax(t4, t5);
     double gap = (lb > 0.0) ? (ub - lb) / lb : (ub - lb) / fmax(fabs(ub), 1e-300);
     out4[0] = t0; out4[1] = ub; out4[2] = lb; out4[3] = gap;
+    if (lb2) { lb2[0] = t4; lb2[1] = t5; }
   }
 }
 void launch_cert_pre(const double* a, const double* r, const double* F, int m, double s,
@@ -557,8 +563,9 @@ void launch_cert_mid(const double* b, const double* c1, int n, double* ys, doubl
 }
 void launch_cert_final(const double* a, const double* b, const double* rr, const double* cr,
                        const double* cp, const double* tc, const double* u2, const double* v,
-                       int m, int n, double* out4, cudaStream_t st) {
-  k_cert_final<<<1, 256, 0, st>>>(a, b, rr, cr, cp, tc, u2, v, m, n, out4);
+                       const double* u2T, const double* vT, int m, int n, double* out4,
+                       double* lb2, cudaStream_t st) {
+  k_cert_final<<<1, 256, 0, st>>>(a, b, rr, cr, cp, tc, u2, v, u2T, vT, m, n, out4, lb2);
 }
 
 // cast helpers

@@ -201,8 +201,8 @@ def pins_step_objective_increase(h, prob, s, F, G, df, dg, alpha, out) -> int:
                                                _ptr(dg), alpha, _ptr(out))
 
 
-def pins_step_certificate(h, prob, s, F, G, out4) -> int:
-    return load().pins_step_certificate(h, ct.byref(prob), s, _ptr(F), _ptr(G), _ptr(out4))
+def pins_step_certificate(h, prob, s, F, G, out6) -> int:
+    return load().pins_step_certificate(h, ct.byref(prob), s, _ptr(F), _ptr(G), _ptr(out6))
 
 
 def pins_marginals_noalloc(prob, eta, prec, s, F, G, r, c, out3, stream=None) -> int:

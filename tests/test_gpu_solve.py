@@ -254,3 +254,65 @@ def test_invalid_inputs_rejected():
         assert pins.pins_poll(h.h, 123456, res2) == pins.PINS_ERR_UNKNOWN_TICKET
     finally:
         h.close()
+
+
+# --------------------------------------------------------------------------- #
+# The accuracy operating point: certified relative gap <= 1e-6 (reading R9)
+# --------------------------------------------------------------------------- #
+def _hi_lp_opt(C, a, b):
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    m, n = C.shape
+    rows = np.concatenate([np.repeat(np.arange(m), n), m + np.tile(np.arange(n), m)])
+    cols = np.concatenate([np.arange(m * n), np.arange(m * n)])
+    A = coo_matrix((np.ones(2 * m * n), (rows, cols)), shape=(m + n, m * n)).tocsr()
+    res = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([a, b * (a.sum() / b.sum())]),
+                  bounds=(0, None), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10,
+                           "dual_feasibility_tolerance": 1e-10})
+    assert res.status == 0
+    return float(res.fun)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_points_instance_certified_to_1e6_at_eta_1e4(prec):
+    """64 x 64 uniform points, random weights (the paper's smallest synthetic
+    size), eta = 1e-4 (Table 3's most accurate setting): both paths stop on a
+    certified relative gap <= 1e-6 within a few outer iterations (s/eta up to
+    ~1e5).  FP64 follows the oracle's iterates (same outer count, cost and
+    bounds within 1e-8); the mixed path solves the FP32-rounded cost and its
+    error to that cost's LP optimum is at most the certified 1e-6."""
+    w = wl.small_points(0)
+    C = w.C if prec == "fp64" else w.C.astype(np.float32).astype(np.float64)
+    kw = dict(eta=1e-4, tol_gap=1e-6, K=250)
+    out = _solve(pins.make_problem("dense", w.a, w.b, C=C if prec == "fp64" else C.astype(np.float32)),
+                 prec=prec, **kw)
+    assert out["status"] == 0 and out["rel_gap"] <= 1e-6
+    opt = _hi_lp_opt(C, w.a, w.b)
+    assert out["dual_lb"] <= opt * (1 + 1e-9) and out["cost_ub"] >= opt * (1 - 1e-9)
+    assert abs(out["cost"] - opt) / opt <= 1.2e-6
+    if prec == "fp64":
+        ref = po.pins(C, w.a, w.b, **kw)
+        assert out["outer_iters"] == ref["outer_iters"]
+        assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= 1e-8
+        assert abs(out["dual_lb"] - ref["lb"]) <= 1e-8 * ref["lb"]
+        assert abs(out["cost_ub"] - ref["ub"]) <= 1e-8 * ref["ub"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stroke_pair_certified_to_1e6(prec):
+    """A 16 x 16 stroke-image pair (grid cost on the fly, eta = 1e-3): integer
+    grid costs give an LP whose reduced costs are multiples of the cost scale, so
+    the plan concentrates quickly and the support-tree bound certifies <= 1e-6.
+    FP64 against the oracle within 1e-8; mixed against the same oracle run."""
+    w = wl.stroke_pair(0, eta=1e-3, s=16)
+    kw = dict(eta=1e-3, tol_gap=1e-6, K=250)
+    out = _solve(pins.problem_from_workload(w), prec=prec, **kw)
+    assert out["status"] == 0 and out["rel_gap"] <= 1e-6
+    ref = po.pins(w.dense_cost(), w.a, w.b, **kw)
+    assert ref["rel_gap"] <= 1e-6
+    tol = 1e-8 if prec == "fp64" else 1e-6
+    assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= tol
+    assert out["dual_lb"] <= ref["ub"] * (1 + 1e-12) and out["cost_ub"] >= ref["lb"] * (1 - 1e-12)
+    if prec == "fp64":
+        assert out["outer_iters"] == ref["outer_iters"]

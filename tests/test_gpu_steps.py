@@ -254,15 +254,81 @@ def test_certificate(handles, prec, m, n):
     import torch
     C, a, b, F, G, eta, s = random_state(m, n, 3 * m + 2 * n)
     prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
     st = pins.pins_step_certificate(handles[prec].h, prob.prob, s, dev(F), dev(G), out)
     assert st == 0, handles[prec].error()
-    cert = po.certificate(C, a, b, F, G, eta, s)
+    Cx = C.astype(np.float32).astype(np.float64) if prec == "mixed" else C
+    cert = po.certificate(Cx, a, b, F, G, eta, s)
     o = out.cpu().numpy()
     tol = 1e-11 if prec == "fp64" else 1e-9
     assert o[0] == pytest.approx(cert["cost"], rel=tol)
     assert o[1] == pytest.approx(cert["ub"], rel=tol)
-    assert o[2] == pytest.approx(cert["lb"], rel=tol, abs=1e-13)
+    assert o[4] == pytest.approx(cert["lb_entropic"], rel=tol, abs=1e-13)
+    assert o[2] == max(o[4], o[5])
+    if prec == "fp64":
+        # same keys, so the same support, forest and potentials as the oracle
+        assert o[5] == pytest.approx(cert["lb_tree"], rel=tol, abs=1e-13)
+        assert o[2] == pytest.approx(cert["lb"], rel=tol, abs=1e-13)
+    else:
+        # the support is selected by FP32 keys: still a valid bound, and close
+        assert o[5] <= _lp_opt(Cx, a, b) * (1 + 1e-12) + 1e-15
+        assert o[5] == pytest.approx(cert["lb_tree"], rel=1e-6, abs=1e-12)
+
+
+def _lp_opt(C, a, b):
+    from scipy.optimize import linprog
+    from scipy.sparse import coo_matrix
+    m, n = C.shape
+    rows = np.concatenate([np.repeat(np.arange(m), n), m + np.tile(np.arange(n), m)])
+    cols = np.concatenate([np.arange(m * n), np.arange(m * n)])
+    A = coo_matrix((np.ones(2 * m * n), (rows, cols)), shape=(m + n, m * n)).tocsr()
+    res = linprog(C.ravel(), A_eq=A, b_eq=np.concatenate([a, b * (a.sum() / b.sum())]),
+                  bounds=(0, None), method="highs")
+    assert res.status == 0
+    return float(res.fun)
+
+
+def _nw_corner_1d(m, n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.uniform(0, 1, size=m))
+    y = np.sort(rng.uniform(0, 1, size=n))
+    a = rng.uniform(0.5, 1.5, size=m); a /= a.sum()
+    b = rng.uniform(0.5, 1.5, size=n); b /= b.sum()
+    C = (x[:, None] - y[None, :]) ** 2
+    C = (C / C.max()).astype(np.float32).astype(np.float64)
+    i = j = 0
+    ra, rb = a.copy(), b.copy()
+    opt = 0.0
+    while i < m and j < n:
+        t = min(ra[i], rb[j])
+        opt += t * C[i, j]
+        ra[i] -= t; rb[j] -= t
+        if ra[i] <= rb[j]:
+            i += 1
+        else:
+            j += 1
+    return C, a, b, opt
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_certificate_tree_bound_reaches_the_optimum(handles, prec):
+    """On a concentrated plan of a non-degenerate instance (1-D, random weights;
+    optimum by the north-west corner rule) the support-tree bound equals OPT to
+    rounding on both paths, far above the entropic-dual bound."""
+    import torch
+    C, a, b, opt = _nw_corner_1d(20, 27, 7)
+    eta = 1e-3
+    res = po.pins(C, a, b, eta=eta, tol_marg=1e-12, K=8)
+    F, G, s = res["F"], res["G"], res["s"]
+    prob = dense_device_problem(C.astype(np.float32) if prec == "mixed" else C, a, b)
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_certificate(handles[prec].h, prob.prob, s, dev(F), dev(G), out)
+    assert st == 0, handles[prec].error()
+    o = out.cpu().numpy()
+    assert abs(o[5] - opt) <= 1e-12 * opt
+    assert o[2] == o[5]
+    assert opt - o[4] > 1e-6 * opt
+    assert o[1] >= opt * (1 - 1e-12)
 
 
 def test_step_rejects_host_pointers(handles):
