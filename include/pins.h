@@ -280,6 +280,23 @@ pins_status pins_step_certificate(pins_handle* h, const pins_problem* p,
                                   double s, const double* F, const double* G,
                                   double* out6);
 
+/* Serving: device bytes the worker pool's arenas hold (reserved for running
+ * requests plus arenas idle workers keep for reuse) and the admission budget.
+ * Admission keeps *held <= *budget, except for a single request running alone.
+ * The handle's own blocking solver (pins_solve, step entry points) is outside
+ * this pool.  The paper has no counterpart: it is serving bookkeeping. */
+pins_status pins_serving_held_bytes(pins_handle* h, size_t* held, size_t* budget);
+
+/* Test hook (the paper has no counterpart): host-side fault injection on this
+ * handle's solvers, so that error paths are tested without faulting a GPU.
+ * The next `alloc_failures` workspace allocations report failure before any
+ * device allocation is attempted (the solve returns PINS_ERR_OOM), and the next
+ * `kernel_errors` line-search checks of the kernels' error word see an error
+ * bit (the solve returns PINS_ERR_CUDA).  Counters are consumed across all of
+ * the handle's solvers (blocking and serving); 0, 0 clears them.  Errors:
+ * PINS_ERR_INVALID_ARG for a NULL handle or negative counts. */
+pins_status pins_test_inject_faults(pins_handle* h, int alloc_failures, int kernel_errors);
+
 /* ------------------------------------------------------------------------- */
 /* Allocation-free marginal pass.  The paper has no counterpart: this entry   */
 /* serves callers that cannot allocate device memory (a host framework that   */

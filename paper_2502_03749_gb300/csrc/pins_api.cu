@@ -4,11 +4,13 @@
 // Serving design: requests are deep-copied into host memory at submit and
 // queued.  A fixed pool of worker threads, each owning one CUDA stream and one
 // Solver (device workspace arena), takes requests in arrival order when (a) the
-// worker is idle and (b) the bytes reserved by running requests plus the new
-// request's workspace fit the device budget.  Running requests overlap on the
-// device through their streams; each keeps its potentials, CSR pattern and CG
-// vectors resident in its own arena for its whole solve.  All kernels reduce in
-// a fixed order, so a result does not depend on what else runs.
+// worker is idle and (b) every arena the pool holds -- those of running
+// requests and those idle workers keep for reuse -- fits the device budget with
+// the new request's workspace.  Idle workers' arenas are released when that is
+// what makes a request fit.  Running requests overlap on the device through
+// their streams; each keeps its potentials, CSR pattern and CG vectors resident
+// in its own arena for its whole solve.  All kernels reduce in a fixed order, so
+// a result does not depend on what else runs.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -63,7 +65,11 @@ struct pins_handle {
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> worker_streams;
-  size_t budget = 0, reserved = 0;
+  std::vector<std::unique_ptr<Solver>> worker_solvers;
+  std::vector<size_t> held;      // per worker: arena bytes held (reserved while running)
+  std::vector<char> busy;        // per worker: running a request
+  pins::FaultHooks hooks;        // host-side fault injection (tests)
+  size_t budget = 0;
   int running = 0;
   bool stopping = false;
   uint64_t next_ticket = 1;
@@ -153,6 +159,7 @@ extern "C" pins_status pins_create(const pins_config* cfg, pins_handle** out) {
   cudaMemcpy(h->exp_table, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice);
   h->solver.reset(new Solver(h->device, h->sms, h->exp_table));
   h->solver->set_stream(h->stream);
+  h->solver->set_hooks(&h->hooks);
   h->solver->set_profile(cfg->profile != 0);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -171,6 +178,7 @@ extern "C" void pins_destroy(pins_handle* h) {
   h->cv_work.notify_all();
   for (auto& t : h->workers) t.join();
   cudaSetDevice(h->device);
+  h->worker_solvers.clear();
   for (auto s : h->worker_streams) cudaStreamDestroy(s);
   h->solver.reset();
   if (h->exp_table) cudaFree(h->exp_table);
@@ -207,11 +215,38 @@ extern "C" pins_status pins_solve(pins_handle* h, const pins_problem* p, pins_re
 // serving
 // ------------------------------------------------------------------------- //
 static size_t job_need(const pins_config& cfg, const pins_problem& p) {
-  int kcap = (int)std::min<long long>((long long)p.m * p.n,
-      std::max(1LL, (long long)llround(cfg.sparsify_gamma * (p.m + p.n - 1))));
-  int kind = (p.kind == PINS_COST_POINTS_SQEUCLID) ? 2 : (p.kind == PINS_COST_GRID_SQEUCLID ? 3 : (int)p.kind);
-  return pins::workspace_bytes(p.m, p.n, kcap, std::max(cfg.T1, 1), kind,
-                               cfg.prec == PINS_PREC_MIXED, true, p.d);
+  return pins::solve_workspace_bytes(cfg, p);
+}
+
+// Admission of the queue's head by worker idx (h->mu held).  The pool holds at
+// most budget bytes of arenas: the other workers' arenas (running, or kept by
+// idle workers for reuse) plus what this worker holds for the request -- its
+// own arena if it is at least the need and at most twice it, else a fresh one
+// of the need.  Idle workers' arenas are released while the pool would exceed
+// the budget.  A request always runs when nothing else is running (submit has
+// rejected any request whose need alone exceeds the budget).  The handle's own
+// blocking solver (pins_solve) is not part of this pool.
+static bool admit(pins_handle* h, int idx, size_t need) {
+  const size_t mine = h->held[idx];
+  size_t others = 0;
+  for (size_t k = 0; k < h->held.size(); ++k)
+    if ((int)k != idx) others += h->held[k];
+  bool keep = mine >= need && mine <= 2 * need;
+  size_t after = keep ? mine : need;
+  for (size_t k = 0; k < h->held.size() && others + after > h->budget; ++k) {
+    if ((int)k == idx || h->busy[k] || h->held[k] == 0) continue;
+    h->worker_solvers[k]->release();
+    others -= h->held[k];
+    h->held[k] = 0;
+  }
+  if (keep && others + after > h->budget && others + need <= h->budget) {
+    keep = false;
+    after = need;
+  }
+  if (others + after > h->budget && h->running > 0) return false;
+  if (!keep && mine > 0) h->worker_solvers[idx]->release();
+  h->held[idx] = after;
+  return true;
 }
 
 static pins_status copy_problem(const pins_problem& p, OwnedProblem& o, std::string& why) {
@@ -243,30 +278,24 @@ static pins_status copy_problem(const pins_problem& p, OwnedProblem& o, std::str
 
 static void worker_main(pins_handle* h, int idx) {
   cudaSetDevice(h->device);
-  Solver solver(h->device, h->sms, h->exp_table);
-  solver.set_stream(h->worker_streams[idx]);
+  Solver& solver = *h->worker_solvers[idx];
   for (;;) {
     std::shared_ptr<Job> job;
     {
       std::unique_lock<std::mutex> lk(h->mu);
       for (;;) {
         if (h->stopping) return;
-        if (!h->queue.empty()) {
-          auto& front = h->queue.front();
-          // admission by device memory (arrival order: the head waits for room)
-          bool fits = h->reserved + front->need <= h->budget || h->running == 0;
-          if (fits) {
-            job = front;
-            h->queue.pop_front();
-            h->reserved += job->need;
-            ++h->running;
-            break;
-          }
+        // admission by device memory (arrival order: the head waits for room)
+        if (!h->queue.empty() && admit(h, idx, h->queue.front()->need)) {
+          job = h->queue.front();
+          h->queue.pop_front();
+          h->busy[idx] = 1;
+          ++h->running;
+          break;
         }
         h->cv_work.wait(lk);
       }
     }
-    if (solver.arena_bytes() > 2 * job->need) solver.release();
     job->prob.F.resize(job->prob.p.m);
     job->prob.G.resize(job->prob.p.n);
     job->res.F_out = job->prob.F.data();
@@ -277,7 +306,8 @@ static void worker_main(pins_handle* h, int idx) {
       job->status = st;
       job->error = solver.error();
       job->done = true;
-      h->reserved -= job->need;
+      h->held[idx] = solver.arena_bytes();
+      h->busy[idx] = 0;
       --h->running;
     }
     h->cv_done.notify_all();
@@ -292,6 +322,11 @@ static void start_workers(pins_handle* h) {
     cudaStream_t s;
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     h->worker_streams.push_back(s);
+    h->worker_solvers.emplace_back(new Solver(h->device, h->sms, h->exp_table));
+    h->worker_solvers.back()->set_stream(s);
+    h->worker_solvers.back()->set_hooks(&h->hooks);
+    h->held.push_back(0);
+    h->busy.push_back(0);
   }
   for (int i = 0; i < h->cfg.max_inflight; ++i) h->workers.emplace_back(worker_main, h, i);
 }
@@ -446,4 +481,25 @@ extern "C" pins_status pins_step_certificate(pins_handle* h, const pins_problem*
   PINS_STEP_GUARD(h, p);
   if (!F || !G || !out6) return PINS_ERR_INVALID_ARG;
   return step_result(h, h->solver->step_certificate(h->cfg, *p, s, F, G, out6));
+}
+
+// ------------------------------------------------------------------------- //
+// test hooks (host-side fault injection)
+// ------------------------------------------------------------------------- //
+extern "C" pins_status pins_test_inject_faults(pins_handle* h, int alloc_failures,
+                                               int kernel_errors) {
+  if (!h || alloc_failures < 0 || kernel_errors < 0) return PINS_ERR_INVALID_ARG;
+  h->hooks.alloc_fail.store(alloc_failures);
+  h->hooks.kernel_error.store(kernel_errors);
+  return PINS_OK;
+}
+
+extern "C" pins_status pins_serving_held_bytes(pins_handle* h, size_t* held, size_t* budget) {
+  if (!h || !held || !budget) return PINS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(h->mu);
+  size_t t = 0;
+  for (size_t v : h->held) t += v;
+  *held = t;
+  *budget = h->budget;
+  return PINS_OK;
 }

@@ -130,6 +130,17 @@ size_t workspace_bytes(int m, int n, int kcap, int t1cap, int cost_kind, bool mi
   return cv.off + 256;
 }
 
+int solve_kcap(const pins_config& cfg, int m, int n) {
+  const long long ksup = 2LL * (m + n - 1);
+  const long long kg = llround(cfg.sparsify_gamma * (m + n - 1));
+  return (int)std::min<long long>((long long)m * n, std::max({1LL, ksup, kg}));
+}
+
+size_t solve_workspace_bytes(const pins_config& cfg, const pins_problem& p) {
+  return workspace_bytes(p.m, p.n, solve_kcap(cfg, p.m, p.n), std::max(cfg.T1, 1), p.kind,
+                         cfg.prec == PINS_PREC_MIXED, true, p.d);
+}
+
 Solver::Solver(int device, int sms, const float2* exp_table)
     : device_(device), sms_(sms), exp_table_(exp_table) {}
 
@@ -219,6 +230,12 @@ pins_status Solver::ensure(int m, int n, int kcap, int t1cap, int kind, bool mix
   if (!ws_.base || need > ws_.bytes) {
     if (ws_.base) { cudaFree(ws_.base); ws_.base = nullptr; ws_.bytes = 0; }
     void* p = nullptr;
+    const bool injected = hooks_ && hooks_->alloc_fail.load() > 0 &&
+                          hooks_->alloc_fail.fetch_sub(1) > 0;
+    if (injected) {
+      err_ = "device allocation of " + std::to_string(need) + " bytes failed (injected)";
+      return PINS_ERR_OOM;
+    }
     if (cudaMalloc(&p, need) != cudaSuccess) {
       cudaGetLastError();
       err_ = "device allocation of " + std::to_string(need) + " bytes failed";
@@ -320,10 +337,8 @@ pins_status Solver::prepare(const pins_config& cfg, const pins_problem& p, bool 
   geom_ = make_geom(m_, n_);
   // the kept entries of a Newton step, and the certificate's support: the
   // 2(m + n - 1) largest entries (reading R9 (ii))
-  const long long ksup = 2LL * (m_ + n_ - 1);
-  int kcap = need_kcap ? (int)std::min<long long>((long long)m_ * n_,
-                                                   std::max({1LL, ksup, (long long)llround(cfg.sparsify_gamma * (m_ + n_ - 1))}))
-                       : (int)std::min<long long>((long long)m_ * n_, ksup);
+  int kcap = need_kcap ? solve_kcap(cfg, m_, n_)
+                       : (int)std::min<long long>((long long)m_ * n_, 2LL * (m_ + n_ - 1));
   int t1cap = std::max(cfg.T1, 1);
   pins_status s = ensure(m_, n_, kcap, t1cap, p.kind, mixed_, !p.on_device, p.d);
   if (s != PINS_OK) return s;
@@ -728,8 +743,11 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
           r.cg_iters += (int)h_scal_[SC_CG];
           int flag = 0;
           std::memcpy(&flag, h_scal_ + SC_FLAG, sizeof(int));
+          if (hooks_ && hooks_->kernel_error.load() > 0 && hooks_->kernel_error.fetch_sub(1) > 0)
+            flag |= 64;
           if (flag) {
-            err_ = std::string((flag & 16) ? "a bulk-copy wait gave up in a Sinkhorn pass"
+            err_ = std::string((flag & 64) ? "kernel error flag (injected by the test hook)"
+                               : (flag & 16) ? "a bulk-copy wait gave up in a Sinkhorn pass"
                                : (flag & 32) ? "certificate: the spanning-forest build did not settle"
                                              : "cg: an index outside the cluster's slices was skipped") +
                    " (flag " + std::to_string(flag) + ")";

@@ -1,6 +1,7 @@
 // Host-side solver of one PINS instance on one CUDA stream (Algorithm 2).
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <string>
 #include <vector>
 #include "../../include/pins.h"
@@ -38,6 +39,19 @@ struct Workspace {
 
 size_t workspace_bytes(int m, int n, int kcap, int t1cap, int cost_kind, bool mixed,
                        bool host_inputs, int d);
+// kept-entry capacity of a full solve: the Newton steps' gamma (m + n - 1) and
+// the certificate's 2 (m + n - 1), at most m n
+int solve_kcap(const pins_config& cfg, int m, int n);
+// device bytes pins_solve needs for problem p (host inputs)
+size_t solve_workspace_bytes(const pins_config& cfg, const pins_problem& p);
+
+// Host-side fault injection for tests: no GPU fault is ever caused.  alloc_fail
+// makes the next workspace allocations report failure before any cudaMalloc;
+// kernel_error makes the next line-search syncs report a kernel error flag.
+struct FaultHooks {
+  std::atomic<int> alloc_fail{0};
+  std::atomic<int> kernel_error{0};
+};
 
 class Solver {
  public:
@@ -52,6 +66,7 @@ class Solver {
   Solver& operator=(const Solver&) = delete;
 
   void set_stream(cudaStream_t s) { stream_ = s; }
+  void set_hooks(FaultHooks* f) { hooks_ = f; }
   cudaStream_t stream() const { return stream_; }
   size_t arena_bytes() const { return ws_.bytes; }
   void release();
@@ -126,6 +141,7 @@ class Solver {
 
   int device_, sms_;
   const float2* exp_table_;
+  FaultHooks* hooks_ = nullptr;
   cudaStream_t stream_ = nullptr;
   Workspace ws_;
   double* h_scal_ = nullptr;   // pinned mirror of ws_.scal

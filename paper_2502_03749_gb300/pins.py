@@ -40,7 +40,8 @@ EXPORTED = ["pins_config_default", "pins_create", "pins_destroy", "pins_last_err
             "pins_solve", "pins_solve_batch", "pins_submit", "pins_poll", "pins_wait",
             "pins_step_sinkhorn", "pins_step_marginals", "pins_step_sparsify", "pins_step_cg",
             "pins_step_objective_increase", "pins_step_certificate", "pins_profile_classes",
-            "pins_profile_name", "pins_profile_read", "pins_marginals_noalloc"]
+            "pins_profile_name", "pins_profile_read", "pins_marginals_noalloc",
+            "pins_serving_held_bytes", "pins_test_inject_faults"]
 
 
 class pins_config(ct.Structure):
@@ -113,6 +114,8 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.pins_profile_name.argtypes = [I]
     lib.pins_profile_read.argtypes = [P, P, P, I, I]
     lib.pins_marginals_noalloc.argtypes = [ct.POINTER(pins_problem), D, I, D, P, P, P, P, P, P]
+    lib.pins_serving_held_bytes.argtypes = [P, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)]
+    lib.pins_test_inject_faults.argtypes = [P, I, I]
     for name in EXPORTED:
         if name not in ("pins_config_default", "pins_destroy", "pins_last_error"):
             getattr(lib, name).restype = ct.c_int
@@ -209,6 +212,19 @@ def pins_marginals_noalloc(prob, eta, prec, s, F, G, r, c, out3, stream=None) ->
     """Allocation-free marginal pass (see include/pins.h); queued on `stream`."""
     return load().pins_marginals_noalloc(ct.byref(prob), eta, prec, s, _ptr(F), _ptr(G),
                                          _ptr(r), _ptr(c), _ptr(out3), stream)
+
+
+def pins_serving_held_bytes(h):
+    """(bytes held by the serving pool's arenas, admission budget)."""
+    held, budget = ct.c_size_t(0), ct.c_size_t(0)
+    st = load().pins_serving_held_bytes(h, ct.byref(held), ct.byref(budget))
+    if st != PINS_OK:
+        raise RuntimeError(f"pins_serving_held_bytes: {STATUS_NAMES.get(st, st)}")
+    return int(held.value), int(budget.value)
+
+
+def pins_test_inject_faults(h, alloc_failures: int, kernel_errors: int) -> int:
+    return load().pins_test_inject_faults(h, alloc_failures, kernel_errors)
 
 
 def pins_profile_classes() -> int:
