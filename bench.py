@@ -83,6 +83,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, metavar="P",
                     help="instead of the contract line: P stroke pairs through pins_solve_batch")
     ap.add_argument("--batch-inflight", type=int, default=8)
+    ap.add_argument("--single", type=int, default=0, metavar="S",
+                    help="instead of the contract line: one mixed solve of the first stroke pair "
+                         "on an S x S grid (a warm-up solve first); the command the kernel "
+                         "profiles under profiles/ capture")
     ap.add_argument("--fp64-seconds", type=float, default=120.0)
     a = ap.parse_args()
     if a.eta is None:
@@ -633,8 +637,33 @@ def run_batch(args):
                       "inflight": args.batch_inflight}), flush=True)
 
 
+def run_single(args):
+    import torch
+    from paper_2502_03749_gb300 import pins, workloads as wl
+    w = next(w for w in (wl.stroke_pair(i, eta=args.eta) for i in range(64))
+             if w.grid[0] == args.single)
+    ref = pins.problem_from_workload(w)
+    h = pins.Pins(**solver_cfg(args, args.prec))
+    try:
+        h.solve(ref, want_potentials=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        d = h.solve(ref, want_potentials=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t
+    finally:
+        h.close()
+    print(json.dumps({"mode": "single", "grid": args.single, "prec": args.prec, "seconds": t,
+                      "rel_gap": d["rel_gap"], "outer_iters": d["outer_iters"],
+                      "newton_iters": d["newton_iters"], "cg_iters": d["cg_iters"],
+                      "gpu_launches": d["gpu_launches"]}), flush=True)
+
+
 def main():
     args = parse()
+    if args.single:
+        run_single(args)
+        return
     if args.lse_roofline:
         print(json.dumps(dict(mode="lse_roofline", **lse_roofline(args, args.lse_roofline))),
               flush=True)

@@ -72,39 +72,77 @@ __global__ void k_csc_place(const int* indptr, const int* indices, const double*
       tval[pos] = data[e];
     }
 }
-// one warp sorts segment j of (tkey, tval) by key into (okey, oval); fill[j] = 0
+// Bitonic sort of up to 32 W (key, value) pairs held W per lane, virtual
+// position p = w * 32 + lane, ascending by key.  Partners closer than 32 are in
+// other lanes (shuffles), farther ones in another register slot of the same lane.
+template <int W>
+__device__ __forceinline__ void warp_bitonic(int (&r)[W], double (&v)[W]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32 * W; k <<= 1) {
+#pragma unroll
+    for (int h = k >> 1; h > 0; h >>= 1) {
+      if (h >= 32) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const int w2 = w ^ (h >> 5);
+          if (w2 > w) {
+            const bool up = ((w * 32 + lane) & k) == 0;
+            if (up ? r[w] > r[w2] : r[w] < r[w2]) {
+              const int tr = r[w]; r[w] = r[w2]; r[w2] = tr;
+              const double tv = v[w]; v[w] = v[w2]; v[w2] = tv;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const int rk = __shfl_xor_sync(0xffffffffu, r[w], h);
+          const double vk = __shfl_xor_sync(0xffffffffu, v[w], h);
+          const bool up = ((w * 32 + lane) & k) == 0, low = (lane & h) == 0;
+          const bool take = low ? (up ? rk < r[w] : rk > r[w]) : (up ? rk > r[w] : rk < r[w]);
+          if (take) { r[w] = rk; v[w] = vk; }
+        }
+      }
+    }
+  }
+}
+template <int W>
+__device__ __forceinline__ void warp_sort_segment(int b, int len, const int* trow,
+                                                  const double* tval, int* rowidx, double* cdata) {
+  const int lane = threadIdx.x & 31;
+  int r[W]; double v[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const int q = w * 32 + lane;
+    r[w] = (q < len) ? trow[b + q] : 0x7fffffff;
+    v[w] = (q < len) ? tval[b + q] : 0.0;
+  }
+  if (len > 1) warp_bitonic<W>(r, v);
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const int q = w * 32 + lane;
+    if (q < len) { rowidx[b + q] = r[w]; cdata[b + q] = v[w]; }
+  }
+}
+// one warp sorts segment j of (trow, tval) by row into (rowidx, cdata); fill[j] = 0.
+// Keys are unique within a segment, so the order is deterministic.
 __device__ __forceinline__ void warp_seg_sort(int j, const int* ptr, int* fill, const int* trow,
                                               const double* tval, int* rowidx, double* cdata) {
   const int lane = threadIdx.x & 31;
-  {
-    const int b = ptr[j], len = ptr[j + 1] - b;
-    if (lane == 0) fill[j] = 0;
-    if (len <= 32) {
-      int r = (lane < len) ? trow[b + lane] : 0x7fffffff;
-      double v = (lane < len) ? tval[b + lane] : 0.0;
-      if (len > 1) {
-#pragma unroll
-        for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-          for (int h = k >> 1; h > 0; h >>= 1) {
-            const int rk = __shfl_xor_sync(0xffffffffu, r, h);
-            const double vk = __shfl_xor_sync(0xffffffffu, v, h);
-            const bool up = (lane & k) == 0, low = (lane & h) == 0;
-            const bool take = low ? (up ? rk < r : rk > r) : (up ? rk > r : rk < r);
-            if (take) { r = rk; v = vk; }
-          }
-        }
-      }
-      if (lane < len) { rowidx[b + lane] = r; cdata[b + lane] = v; }
-    } else {
-      // long column: each entry's rank is the number of smaller rows
-      for (int q = lane; q < len; q += 32) {
-        const int r = trow[b + q];
-        int rank = 0;
-        for (int t = 0; t < len; ++t) rank += (trow[b + t] < r) ? 1 : 0;
-        rowidx[b + rank] = r;
-        cdata[b + rank] = tval[b + q];
-      }
+  const int b = ptr[j], len = ptr[j + 1] - b;
+  if (lane == 0) fill[j] = 0;
+  if (len <= 32) warp_sort_segment<1>(b, len, trow, tval, rowidx, cdata);
+  else if (len <= 64) warp_sort_segment<2>(b, len, trow, tval, rowidx, cdata);
+  else if (len <= 128) warp_sort_segment<4>(b, len, trow, tval, rowidx, cdata);
+  else {
+    // long segment: each entry's rank is the number of smaller rows
+    for (int q = lane; q < len; q += 32) {
+      const int r = trow[b + q];
+      int rank = 0;
+      for (int t = 0; t < len; ++t) rank += (trow[b + t] < r) ? 1 : 0;
+      rowidx[b + rank] = r;
+      cdata[b + rank] = tval[b + q];
     }
   }
 }
