@@ -6,7 +6,7 @@ Default workload: a served stream of stroke-image pairs -- the shapes of the
 paper's augmented-MNIST family (Section 5.1.1): 1-3 thick polylines, shifted or
 rotated, on grids drawn uniformly from 16^2 ... 64^2, squared pixel distance
 normalised to max 1, the cost generated from grid indices and never stored.
-Every request asks for a certified relative gap <= 1e-6 (eta = 1e-3, K <= 250,
+Every request asks for a certified relative gap <= 1e-6 (eta = 2.5e-4, K <= 250,
 sparsify budget 2 (m + n - 1)); a request counts as solved only when its
 certificate meets the target.  One step = one stream of R requests arriving as
 a Poisson process, admitted into the library's serving pool (continuous
@@ -57,14 +57,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="strokes", choices=["strokes", "gmm4096"])
     ap.add_argument("--eta", type=float, default=None,
-                    help="default 1e-3 (strokes), 1e-2 (gmm4096)")
+                    help="default 2.5e-4 (strokes), 1e-2 (gmm4096)")
     ap.add_argument("--K", type=int, default=250)
     ap.add_argument("--gamma", type=float, default=None,
                     help="sparsify budget multiplier: default 2 (strokes), 1 (gmm4096)")
     ap.add_argument("--requests", type=int, default=24, help="requests per stream (one step)")
     ap.add_argument("--rate", type=float, default=100.0,
                     help="Poisson arrival rate of the headline stream (req/s)")
-    ap.add_argument("--inflight", type=int, default=8, help="serving slots (max_inflight)")
+    ap.add_argument("--inflight", type=int, default=12, help="serving slots (max_inflight)")
     ap.add_argument("--sweep", default="0.5,1,2,4",
                     help="arrival rates of the saturation sweep ('' to skip)")
     ap.add_argument("--sweep-requests", type=int, default=16)
@@ -90,7 +90,7 @@ def parse():
     ap.add_argument("--fp64-seconds", type=float, default=120.0)
     a = ap.parse_args()
     if a.eta is None:
-        a.eta = 1e-3 if a.workload == "strokes" else 1e-2
+        a.eta = 2.5e-4 if a.workload == "strokes" else 1e-2
     if a.gamma is None:
         a.gamma = 2.0 if a.workload == "strokes" else 1.0
     return a

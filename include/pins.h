@@ -72,10 +72,11 @@ typedef enum {
   /* m x n passes on the FP32 units: the Sinkhorn warm-up uses FP32 exp on a
    * double-float (compensated) exponent; the gradient, line-search, stopping and
    * certificate passes use a double-float table-driven exp (~1e-13 relative).
-   * The CG keeps its vectors and matrix-vector product in double-float (about
-   * 48 significand bits) with FP32 inner products, which steer only its step
-   * lengths.  Potentials, the outer update and the stopping decisions stay
-   * FP64.  A dense FP64 cost is rounded to FP32 once. */
+   * The CG keeps its vectors, matrix-vector product and inner products in
+   * double-float (about 48 significand bits) and checks the true residual
+   * rhs - M x when its recurrence meets the tolerance.  Potentials, the outer
+   * update and the stopping decisions stay FP64.  A dense FP64 cost is rounded
+   * to FP32 once. */
   PINS_PREC_MIXED = 1
 } pins_precision;
 
@@ -241,10 +242,11 @@ pins_status pins_step_sparsify(pins_handle* h, const pins_problem* p, double s,
  * Eq. eq:eppa-hess).  S is CSR (indptr m+1, indices/data nnz).  rhs, d: m + n
  * device doubles.  info (device, 2 doubles) = {iterations, relative residual}.
  * On a PINS_PREC_FP64 handle every operation is FP64.  On a PINS_PREC_MIXED
- * handle the vectors and the matrix-vector product are kept in double-float
- * (FP32 pairs, ~48 significand bits) and the three inner products of each
- * iteration are FP32 sums; the relative residual is then the FP32-measured
- * ||r|| / ||rhs||. */
+ * handle the vectors, the matrix-vector product and the inner products are
+ * kept in double-float (FP32 pairs, ~48 significand bits); when the recurrence
+ * residual meets rtol, the true residual rhs - M d is formed and, if it is
+ * above 2 rtol ||rhs||, the iteration restarts from d (at most three times).
+ * info[1] is then the last measured ||r|| / ||rhs||. */
 pins_status pins_step_cg(pins_handle* h, int m, int n, double eta,
                          const double* r, const double* c, const int* indptr,
                          const int* indices, const double* data, int nnz,
@@ -290,12 +292,16 @@ pins_status pins_serving_held_bytes(pins_handle* h, size_t* held, size_t* budget
 /* Test hook (the paper has no counterpart): host-side fault injection on this
  * handle's solvers, so that error paths are tested without faulting a GPU.
  * The next `alloc_failures` workspace allocations report failure before any
- * device allocation is attempted (the solve returns PINS_ERR_OOM), and the next
+ * device allocation is attempted (the solve returns PINS_ERR_OOM); the next
  * `kernel_errors` line-search checks of the kernels' error word see an error
- * bit (the solve returns PINS_ERR_CUDA).  Counters are consumed across all of
- * the handle's solvers (blocking and serving); 0, 0 clears them.  Errors:
- * PINS_ERR_INVALID_ARG for a NULL handle or negative counts. */
-pins_status pins_test_inject_faults(pins_handle* h, int alloc_failures, int kernel_errors);
+ * bit (the solve returns PINS_ERR_CUDA); the next `selection_failures`
+ * one-pass selections of the mixed path read as failed, so their Newton steps
+ * are redone with the histogram search (the result is unchanged).  Counters
+ * are consumed across all of the handle's solvers (blocking and serving);
+ * zeros clear them.  Errors: PINS_ERR_INVALID_ARG for a NULL handle or
+ * negative counts. */
+pins_status pins_test_inject_faults(pins_handle* h, int alloc_failures, int kernel_errors,
+                                    int selection_failures);
 
 /* ------------------------------------------------------------------------- */
 /* Allocation-free marginal pass.  The paper has no counterpart: this entry   */

@@ -487,10 +487,12 @@ extern "C" pins_status pins_step_certificate(pins_handle* h, const pins_problem*
 // test hooks (host-side fault injection)
 // ------------------------------------------------------------------------- //
 extern "C" pins_status pins_test_inject_faults(pins_handle* h, int alloc_failures,
-                                               int kernel_errors) {
-  if (!h || alloc_failures < 0 || kernel_errors < 0) return PINS_ERR_INVALID_ARG;
+                                               int kernel_errors, int selection_failures) {
+  if (!h || alloc_failures < 0 || kernel_errors < 0 || selection_failures < 0)
+    return PINS_ERR_INVALID_ARG;
   h->hooks.alloc_fail.store(alloc_failures);
   h->hooks.kernel_error.store(kernel_errors);
+  h->hooks.select_fail.store(selection_failures);
   return PINS_OK;
 }
 

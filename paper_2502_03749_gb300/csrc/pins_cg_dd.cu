@@ -4,13 +4,17 @@
 //
 // Why double-float: this GPU issues FP64 at ~1/70 of its FP32 rate, and a CG
 // iteration on a few thousand unknowns is a chain of short dependent steps, so
-// FP64 latency sets its length.  Every vector and the matrix-vector product
-// (diagonal and S entries scaled by 1/eta) keep ~48 significand bits; only the
-// three inner products per iteration (r.u, w.u, r.r) are FP32 sums, which
-// perturb the step lengths alpha, beta by ~1e-6 relatively and so change the
-// rate, not the fixed point.  The preconditioner is D^-1 with D^-1 rounded to
-// FP32 (a fixed diagonal).  rhs is scaled by a power of two (exact) so that its
-// largest entry is in [1, 2); x is scaled back at the end.
+// FP64 latency sets its length.  Every vector, the matrix-vector product
+// (diagonal and S entries scaled by 1/eta) and the three inner products per
+// iteration (r.u, w.u, r.r) keep ~48 significand bits; the step lengths alpha,
+// beta are formed in FP64 from them and applied as FP32 scalars (the same value
+// in every recurrence, so the recurrences stay consistent).  FP32 inner
+// products, measured on the Newton systems of 64 x 64 grid problems, doubled
+// the iteration count against FP64 CG and let the recurrence residual drift
+// from the true one by two orders of magnitude.  The preconditioner is D^-1
+// with D^-1 rounded to FP32 (a fixed diagonal).  rhs is scaled by a power of
+// two (exact) so that its largest entry is in [1, 2); x is scaled back at the
+// end.
 //
 // Ordering: the pipelined PCG of Ghysels & Vanroose (Parallel Computing 40,
 // 2014), which puts the one global reduction of an iteration and its
@@ -48,6 +52,9 @@ namespace pins {
 #define PINS_DDCG_SLICE 256
 // shared bytes per unknown: x, r, u, w, z, q, s, p, m, diag, od (11 x 8) + D^-1 (4) + row begin (4)
 #define PINS_DDCG_PER_UNKNOWN 96
+// passes of the CG: the first, and restarts from x when the true residual at
+// the end of a pass is above twice the tolerance
+#define PINS_DDCG_PASSES 4
 
 struct CGddArgs {
   int m, n;
@@ -62,7 +69,7 @@ struct CGddArgs {
   int* ent_row;
   float* ug;                       // u of every unknown (N floats), the exchange buffer
   size_t smem_bytes;               // dynamic shared memory of the launch
-  float rtol2; int max_iter; double* info;
+  double rtol2; int max_iter; double* info;
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
 };
 
@@ -72,11 +79,11 @@ template <bool LOCAL>
 __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
-  __shared__ float slot[2][3][PINS_DDCG_MAX];     // double-buffered block partials
+  __shared__ float2 slot[2][3][PINS_DDCG_MAX];    // double-buffered block partials
   __shared__ unsigned int eslot[1];
   __shared__ double dred[2][PINS_DDCG_TPB / 32];
   __shared__ double dslot[2][PINS_DDCG_MAX];
-  __shared__ float red[3][PINS_DDCG_TPB / 32];
+  __shared__ float2 red[3][PINS_DDCG_TPB / 32];
   __shared__ unsigned int ered[PINS_DDCG_TPB / 32];
   __shared__ int hrow[PINS_DDCG_TPB];
   __shared__ float2 hval[PINS_DDCG_TPB];
@@ -180,14 +187,10 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   unsigned int E = 0u;
   for (int q = 0; q < CS; ++q) E = max(E, *cluster.map_shared_rank(eslot, q));
   const int shift = (int)E - 1023;                  // max |rhs| 2^-shift in [1, 2)
-  // r0 = rhs (scaled), u0 = D^-1 r0, published in exchange buffer 1 for w0 = M u0
+  // r0 = rhs (scaled) and x0 = 0 for the first pass
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-    const float2 r0 = split_f64(rhs_of(lo + k), shift);
-    rv[k] = r0;
-    const float2 u0 = ddv_scale(dinv[k], r0);
-    uv[k] = u0;
-    mv[k] = u0;
-    if (!LOCAL) __stcg(mg + N + lo + k, u0);
+    rv[k] = split_f64(rhs_of(lo + k), shift);
+    xv[k] = make_float2(0.f, 0.f);
   }
   // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
   const int ne = E1 - E0;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // Products first (independent), then a sum over runs of equal local row; a
   // row cut by the slice start is this thread's head, a row cut by its end its
   // tail (completed below from the following threads' heads, in thread order).
-  auto spmv = [&](const float2* src) {
+  auto spmv = [&](const float2* src, const float2* lsrc) {
     float2 headv = make_float2(0.f, 0.f), tailv = make_float2(0.f, 0.f);
     int headrow = -1, tailrow = -1;
     if (c0 < c1) {
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
           rw[q] = ok ? erow[base + q] : cur;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) uu[q] = LOCAL ? mv[tg[q]] : __ldcg(src + tg[q]);
+        for (int q = 0; q < 4; ++q) uu[q] = LOCAL ? lsrc[tg[q]] : __ldcg(src + tg[q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           two_prod(v[q].x, uu[q].x, ph[q], pl[q]);
@@ -265,30 +268,30 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     }
     __syncthreads();
   };
-  // three block partials -> slot buffer `b` of every CTA (the cluster barrier
-  // that follows publishes them)
-  auto publish3 = [&](float v0, float v1, float v2, int b) {
+  // three block partials (double-float) -> slot buffer `b` of every CTA (the
+  // cluster barrier that follows publishes them)
+  auto warp_sum2 = [&](float2 v) -> float2 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-      v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+      const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                                   __shfl_xor_sync(0xffffffffu, v.y, o));
+      v = ddv_add(v, w);
     }
+    return v;
+  };
+  auto norm2 = [](float2 v) { float h, l; fast_two_sum(v.x, v.y, h, l); return make_float2(h, l); };
+  auto publish3 = [&](float2 v0, float2 v1, float2 v2, int b) {
+    v0 = warp_sum2(norm2(v0)); v1 = warp_sum2(norm2(v1)); v2 = warp_sum2(norm2(v2));
     if (lane == 0) { red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; }
     __syncthreads();
     if (warp == 0) {
       constexpr int W = PINS_DDCG_TPB / 32;
-      float b0 = lane < W ? red[0][lane] : 0.f;
-      float b1 = lane < W ? red[1][lane] : 0.f;
-      float b2 = lane < W ? red[2][lane] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        b0 += __shfl_xor_sync(0xffffffffu, b0, o);
-        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
-        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-      }
+      const float2 z = make_float2(0.f, 0.f);
+      float2 b0 = warp_sum2(lane < W ? red[0][lane] : z);
+      float2 b1 = warp_sum2(lane < W ? red[1][lane] : z);
+      float2 b2 = warp_sum2(lane < W ? red[2][lane] : z);
       if (lane < CS) {
-        float* rs = cluster.map_shared_rank(&slot[b][0][0], lane);
+        float2* rs = cluster.map_shared_rank(&slot[b][0][0], lane);
         rs[0 * PINS_DDCG_MAX + rank] = b0;
         rs[1 * PINS_DDCG_MAX + rank] = b1;
         rs[2 * PINS_DDCG_MAX + rank] = b2;
@@ -296,100 +299,156 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     }
   };
   // every warp sums the slots of buffer `b` in the same butterfly order
-  // (bit-identical in all lanes and CTAs)
-  auto gather3 = [&](int b, float& t0r, float& t1r, float& t2r) {
-    float q0 = lane < CS ? slot[b][0][lane] : 0.f;
-    float q1 = lane < CS ? slot[b][1][lane] : 0.f;
-    float q2 = lane < CS ? slot[b][2][lane] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      q0 += __shfl_xor_sync(0xffffffffu, q0, o);
-      q1 += __shfl_xor_sync(0xffffffffu, q1, o);
-      q2 += __shfl_xor_sync(0xffffffffu, q2, o);
-    }
+  // (bit-identical in all lanes and CTAs) and converts the totals to FP64
+  auto gather3 = [&](int b, float2& t0r, float2& t1r, float2& t2r) {
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 q0 = warp_sum2(lane < CS ? slot[b][0][lane] : z);
+    const float2 q1 = warp_sum2(lane < CS ? slot[b][1][lane] : z);
+    const float2 q2 = warp_sum2(lane < CS ? slot[b][2][lane] : z);
     t0r = q0; t1r = q1; t2r = q2;
   };
 
-  // (r.u, w.u, r.r) partials and m = D^-1 w of the own unknown k, m published in
-  // exchange buffer b (the next iteration's phase A, fused into the vector updates)
-  auto phase_a = [&](int k, float2 w, float rk, float uk, int b, float& lg, float& ld,
-                     float& lrr) {
-    lg = __fmaf_rn(rk, uk, lg);
-    ld = __fmaf_rn(w.x, uk, ld);
-    lrr = __fmaf_rn(rk, rk, lrr);
+  // (r.u, w.u, r.r) partials (double-float products and sums) and m = D^-1 w of
+  // the own unknown k, m published in exchange buffer b (the next iteration's
+  // phase A, fused into the vector updates)
+  // acc += x y for double-float x, y, accumulated unnormalised (hi by TwoSum,
+  // every lower-order term into lo); normalised once in the reductions below
+  auto acc2 = [](float2& acc, float2 x, float2 y) {
+    float p, e; two_prod(x.x, y.x, p, e);
+    e = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
+    float sh, st; two_sum(acc.x, p, sh, st);
+    acc.x = sh; acc.y = __fadd_rn(acc.y, __fadd_rn(st, e));
+  };
+  auto phase_a = [&](int k, float2 w, float2 rk, float2 uk, int b, float2& lg, float2& ld,
+                     float2& lrr) {
+    acc2(lg, rk, uk);
+    acc2(ld, w, uk);
+    acc2(lrr, rk, rk);
     const float2 mk = ddv_scale(dinv[k], w);
     mv[k] = mk;
     if (!LOCAL) __stcg(mg + (size_t)b * N + lo + k, mk);
   };
 
-  // w0 = M u0, then phase A of the first iteration
-  cluster.sync();                                   // every u0 slice published
-  spmv(mg + N);
+  // Passes: pipelined PCG from (x, r) until the recurrence residual meets the
+  // tolerance; then the true residual rhs - M x is formed (one more exchange and
+  // SpMV).  If it is above twice the tolerance -- the recurrences of a long run
+  // can drift from it -- the next pass restarts from x with r = rhs - M x.
+  // the scalar recurrences run in double-float on the FP32 units: FP64 on this
+  // GPU issues at ~1/64 of the FP32 rate and every thread forms the scalars
+  const float tol2 = (float)a.rtol2;
+  float2 bb = make_float2(0.f, 0.f), rr = bb;
   int it = 0, buf = 0;
-  float lg = 0.f, ld = 0.f, lrr = 0.f;
-  for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-    const float2 w = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
-    wv[k] = w;
-    od[k] = make_float2(0.f, 0.f);
-    phase_a(k, w, rv[k].x, uv[k].x, buf, lg, ld, lrr);
-  }
-  float gam_prev = 1.f, alpha_prev = 1.f, bb = 0.f, rr = 0.f;
-  while (true) {
-    publish3(lg, ld, lrr, buf);
-    cluster.sync();                                 // m slices and partials published
-    // phase B: scalars (identical in every CTA), then n = M m
-    float gam, dlt;
-    gather3(buf, gam, dlt, rr);
-    if (it == 0) bb = rr;
-    if (!(bb > 0.f) || !(rr > a.rtol2 * bb) || it >= a.max_iter) break;   // NaN stops
-    // the step lengths only steer the iteration (r and x stay consistent for any
-    // value), so the fast FP32 division is enough
-    const float beta = (it == 0) ? 0.f : __fdividef(gam, gam_prev);
-    const float alpha = (it == 0) ? __fdividef(gam, dlt)
-                                  : __fdividef(gam, dlt - beta * __fdividef(gam, alpha_prev));
-    spmv(mg + (size_t)buf * N);
-    // two unknowns per step, loads first, so their dependency chains overlap;
-    // phase A of the next iteration follows each unknown's update (the same
-    // summation order as a separate pass over k = tid, tid + TPB, ...)
-    const int nb = buf ^ 1;
-    lg = 0.f; ld = 0.f; lrr = 0.f;
-    for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
-      const int k2 = k + PINS_DDCG_TPB;
-      const bool two = k2 < nl;
-      const int kk[2] = {k, two ? k2 : k};
-      float2 n0[2], z0[2], q0[2], s0[2], p0[2], x0[2], r0[2], u0[2], w0[2], m0[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int t = kk[h];
-        n0[h] = ddv_add(ddv_mul(dg[t], mv[t]), od[t]);
-        z0[h] = zv[t]; q0[h] = qv[t]; s0[h] = sv[t]; p0[h] = pv[t];
-        x0[h] = xv[t]; r0[h] = rv[t]; u0[h] = uv[t]; w0[h] = wv[t]; m0[h] = mv[t];
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        z0[h] = ddv_axpy(beta, z0[h], n0[h]);
-        q0[h] = ddv_axpy(beta, q0[h], m0[h]);
-        s0[h] = ddv_axpy(beta, s0[h], w0[h]);
-        p0[h] = ddv_axpy(beta, p0[h], u0[h]);
-        x0[h] = ddv_axpy(alpha, p0[h], x0[h]);
-        r0[h] = ddv_axpy(-alpha, s0[h], r0[h]);
-        u0[h] = ddv_axpy(-alpha, q0[h], u0[h]);
-        w0[h] = ddv_axpy(-alpha, z0[h], w0[h]);
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !two) break;
-        const int t = kk[h];
-        od[t] = make_float2(0.f, 0.f);
-        zv[t] = z0[h]; qv[t] = q0[h]; sv[t] = s0[h]; pv[t] = p0[h];
-        xv[t] = x0[h]; rv[t] = r0[h]; uv[t] = u0[h]; wv[t] = w0[h];
-        phase_a(t, w0[h], r0[h].x, u0[h].x, nb, lg, ld, lrr);
-      }
+  bool conv = false;
+  for (int pass = 0; pass < PINS_DDCG_PASSES; ++pass) {
+    // u0 = D^-1 r0 published in exchange buffer 1 for w0 = M u0; z, q, s, p = 0
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float2 u0 = ddv_scale(dinv[k], rv[k]);
+      uv[k] = u0;
+      mv[k] = u0;
+      zv[k] = make_float2(0.f, 0.f);
+      qv[k] = make_float2(0.f, 0.f);
+      sv[k] = make_float2(0.f, 0.f);
+      pv[k] = make_float2(0.f, 0.f);
+      if (!LOCAL) __stcg(mg + N + lo + k, u0);
     }
-    gam_prev = gam;
-    alpha_prev = alpha;
-    ++it;
-    buf = nb;
+    cluster.sync();                                 // every u0 slice published
+    spmv(mg + N, mv);
+    buf = 0;
+    float2 lg = make_float2(0.f, 0.f), ld = lg, lrr = lg;
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float2 w = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
+      wv[k] = w;
+      od[k] = make_float2(0.f, 0.f);
+      phase_a(k, w, rv[k], uv[k], buf, lg, ld, lrr);
+    }
+    float2 gam_prev = make_float2(1.f, 0.f), alpha_prev = gam_prev;
+    int itr = 0;
+    conv = false;
+    while (true) {
+      publish3(lg, ld, lrr, buf);
+      cluster.sync();                               // m slices and partials published
+      // phase B: scalars (identical in every CTA), then n = M m
+      float2 gam, dlt;
+      gather3(buf, gam, dlt, rr);
+      if (pass == 0 && itr == 0) bb = rr;
+      if (!(bb.x > 0.f)) break;
+      if (!(rr.x > tol2 * bb.x)) { conv = true; break; }
+      if (!(rr.x == rr.x) || it >= a.max_iter) break;   // NaN or the cap stops
+      // beta = gam / gam', alpha = gam / (dlt - beta gam / alpha'); the
+      // difference can cancel, so it is formed in double-float
+      const float2 beta = (itr == 0) ? make_float2(0.f, 0.f) : ddv_div(gam, gam_prev);
+      const float2 den = (itr == 0) ? dlt
+                                    : ddv_add(dlt, ddv_neg(ddv_div(ddv_mul(beta, gam), alpha_prev)));
+      const float2 alpha = ddv_div(gam, den);
+      const float bf = beta.x + beta.y, af = alpha.x + alpha.y;
+      spmv(mg + (size_t)buf * N, mv);
+      // two unknowns per step, loads first, so their dependency chains overlap;
+      // phase A of the next iteration follows each unknown's update (the same
+      // summation order as a separate pass over k = tid, tid + TPB, ...)
+      const int nb = buf ^ 1;
+      lg = make_float2(0.f, 0.f); ld = lg; lrr = lg;
+      for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
+        const int k2 = k + PINS_DDCG_TPB;
+        const bool two = k2 < nl;
+        const int kk[2] = {k, two ? k2 : k};
+        float2 n0[2], z0[2], q0[2], s0[2], p0[2], x0[2], r0[2], u0[2], w0[2], m0[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int t = kk[h];
+          n0[h] = ddv_add(ddv_mul(dg[t], mv[t]), od[t]);
+          z0[h] = zv[t]; q0[h] = qv[t]; s0[h] = sv[t]; p0[h] = pv[t];
+          x0[h] = xv[t]; r0[h] = rv[t]; u0[h] = uv[t]; w0[h] = wv[t]; m0[h] = mv[t];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          z0[h] = ddv_axpy(bf, z0[h], n0[h]);
+          q0[h] = ddv_axpy(bf, q0[h], m0[h]);
+          s0[h] = ddv_axpy(bf, s0[h], w0[h]);
+          p0[h] = ddv_axpy(bf, p0[h], u0[h]);
+          x0[h] = ddv_axpy(af, p0[h], x0[h]);
+          r0[h] = ddv_axpy(-af, s0[h], r0[h]);
+          u0[h] = ddv_axpy(-af, q0[h], u0[h]);
+          w0[h] = ddv_axpy(-af, z0[h], w0[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !two) break;
+          const int t = kk[h];
+          od[t] = make_float2(0.f, 0.f);
+          zv[t] = z0[h]; qv[t] = q0[h]; sv[t] = s0[h]; pv[t] = p0[h];
+          xv[t] = x0[h]; rv[t] = r0[h]; uv[t] = u0[h]; wv[t] = w0[h];
+          phase_a(t, w0[h], r0[h], u0[h], nb, lg, ld, lrr);
+        }
+      }
+      gam_prev = gam;
+      alpha_prev = alpha;
+      ++it;
+      ++itr;
+      buf = nb;
+    }
+    if (!conv || pass + 1 == PINS_DDCG_PASSES) break;
+    // true residual t = rhs - M x: x goes through the exchange buffer nobody reads
+    // now (buffer buf ^ 1 was last read before the barrier that ended the loop)
+    const int xb = buf ^ 1;
+    if (!LOCAL)
+      for (int k = tid; k < nl; k += PINS_DDCG_TPB) __stcg(mg + (size_t)xb * N + lo + k, xv[k]);
+    cluster.sync();                                 // x slices published, slots gathered
+    spmv(mg + (size_t)xb * N, xv);
+    float2 lt = make_float2(0.f, 0.f);
+    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+      const float2 mx = ddv_add(ddv_mul(dg[k], xv[k]), od[k]);
+      od[k] = make_float2(0.f, 0.f);
+      const float2 t = ddv_add(split_f64(rhs_of(lo + k), shift), make_float2(-mx.x, -mx.y));
+      rv[k] = t;
+      acc2(lt, t, t);
+    }
+    publish3(lt, make_float2(0.f, 0.f), make_float2(0.f, 0.f), buf);
+    cluster.sync();
+    float2 tt, d1, d2;
+    gather3(buf, tt, d1, d2);
+    rr = tt;
+    if (!(tt.x > 4.f * tol2 * bb.x)) break;         // within twice the tolerance
+    conv = false;
   }
   const double scale = ldexp(1.0, shift);
   double dg0 = 0.0, dg1 = 0.0;                      // <rhs, x>, <ab, x> partials
@@ -416,7 +475,8 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   }
   if (rank == 0 && tid == 0) {
     a.info[0] = (double)it;
-    a.info[1] = (bb > 0.f) ? sqrt((double)rr / (double)bb) : 0.0;
+    const double rrd = (double)rr.x + (double)rr.y, bbd = (double)bb.x + (double)bb.y;
+    a.info[1] = (bbd > 0.0) ? sqrt(rrd / bbd) : 0.0;
   }
   cluster.sync();                                   // no CTA exits while others read its u
   if (a.dots && rank == 0 && tid == 0) {
@@ -494,7 +554,7 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
   a.ent_tgt = ent_tgt; a.ent_val = ent_val; a.ent_row = ent_row;
   a.ug = ug;
   a.smem_bytes = smem;
-  a.rtol2 = (float)(rtol * rtol); a.max_iter = max_iter; a.info = info; a.flag = flag;
+  a.rtol2 = rtol * rtol; a.max_iter = max_iter; a.info = info; a.flag = flag;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(CS);
   lc.blockDim = dim3(PINS_DDCG_TPB);

@@ -106,6 +106,18 @@ __device__ __forceinline__ float2 ddv_scale(float f, float2 v) {
   float h, l; fast_two_sum(p, e, h, l);
   return make_float2(h, l);
 }
+__device__ __forceinline__ float2 ddv_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// a / b for double-float a, b: the FP32 quotient of the leading parts corrected
+// by the remainder a - q b (formed exactly by TwoProduct), normalised
+__device__ __forceinline__ float2 ddv_div(float2 a, float2 b) {
+  const float q1 = __fdiv_rn(a.x, b.x);
+  float p, e; two_prod(q1, b.x, p, e);
+  e = __fmaf_rn(q1, b.y, e);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), e), a.y);
+  const float q2 = __fdiv_rn(r, b.x);
+  float h, l; fast_two_sum(q1, q2, h, l);
+  return make_float2(h, l);
+}
 // y + f * v  (f FP32, v and y double-float), normalised
 __device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
   float p, e; two_prod(f, v.x, p, e);

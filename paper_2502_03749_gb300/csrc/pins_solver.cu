@@ -727,6 +727,9 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         if (q == 0 && fast) {
           FastSelState f;
           std::memcpy(&f, h_scal_ + SC_FAST, sizeof(f));
+          if (!f.fail && hooks_ && hooks_->select_fail.load() > 0 &&
+              hooks_->select_fail.fetch_sub(1) > 0)
+            f.fail = 2;
           if (f.fail) {
             // too few (1) or too many (2) candidates: widen or narrow the margin;
             // too many ties (3) or inconsistent counts: the histogram path

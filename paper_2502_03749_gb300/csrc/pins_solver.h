@@ -47,10 +47,13 @@ size_t solve_workspace_bytes(const pins_config& cfg, const pins_problem& p);
 
 // Host-side fault injection for tests: no GPU fault is ever caused.  alloc_fail
 // makes the next workspace allocations report failure before any cudaMalloc;
-// kernel_error makes the next line-search syncs report a kernel error flag.
+// kernel_error makes the next line-search syncs report a kernel error flag;
+// select_fail makes the next one-pass selections read as failed, so the step is
+// redone by the histogram search.
 struct FaultHooks {
   std::atomic<int> alloc_fail{0};
   std::atomic<int> kernel_error{0};
+  std::atomic<int> select_fail{0};
 };
 
 class Solver {

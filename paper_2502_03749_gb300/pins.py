@@ -115,7 +115,7 @@ def load(path: str = LIB_PATH) -> ct.CDLL:
     lib.pins_profile_read.argtypes = [P, P, P, I, I]
     lib.pins_marginals_noalloc.argtypes = [ct.POINTER(pins_problem), D, I, D, P, P, P, P, P, P]
     lib.pins_serving_held_bytes.argtypes = [P, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)]
-    lib.pins_test_inject_faults.argtypes = [P, I, I]
+    lib.pins_test_inject_faults.argtypes = [P, I, I, I]
     for name in EXPORTED:
         if name not in ("pins_config_default", "pins_destroy", "pins_last_error"):
             getattr(lib, name).restype = ct.c_int
@@ -223,8 +223,9 @@ def pins_serving_held_bytes(h):
     return int(held.value), int(budget.value)
 
 
-def pins_test_inject_faults(h, alloc_failures: int, kernel_errors: int) -> int:
-    return load().pins_test_inject_faults(h, alloc_failures, kernel_errors)
+def pins_test_inject_faults(h, alloc_failures: int, kernel_errors: int,
+                            selection_failures: int = 0) -> int:
+    return load().pins_test_inject_faults(h, alloc_failures, kernel_errors, selection_failures)
 
 
 def pins_profile_classes() -> int:

@@ -300,16 +300,19 @@ def test_points_instance_certified_to_1e6_at_eta_1e4(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_stroke_pair_certified_to_1e6(prec):
-    """A 16 x 16 stroke-image pair (grid cost on the fly, eta = 1e-3): integer
-    grid costs give an LP whose reduced costs are multiples of the cost scale, so
-    the plan concentrates quickly and the support-tree bound certifies <= 1e-6.
-    FP64 against the oracle within 1e-8; mixed against the same oracle run."""
-    w = wl.stroke_pair(0, eta=1e-3, s=16)
-    kw = dict(eta=1e-3, tol_gap=1e-6, K=250)
-    out = _solve(pins.problem_from_workload(w), prec=prec, **kw)
+@pytest.mark.parametrize("eta,gamma", [(1e-3, 1.0), (2.5e-4, 2.0)])
+def test_stroke_pair_certified_to_1e6(prec, eta, gamma):
+    """A 16 x 16 stroke-image pair (grid cost on the fly): integer grid costs give
+    an LP whose reduced costs are multiples of the cost scale, so the plan
+    concentrates and the support-tree bound certifies <= 1e-6, at the paper's
+    sparsify budget and at the benchmark's setting (eta = 2.5e-4, budget
+    2 (m + n - 1)).  FP64 against the oracle within 1e-8; mixed against the same
+    oracle run."""
+    w = wl.stroke_pair(0, eta=eta, s=16)
+    kw = dict(eta=eta, tol_gap=1e-6, K=250)
+    out = _solve(pins.problem_from_workload(w), prec=prec, sparsify_gamma=gamma, **kw)
     assert out["status"] == 0 and out["rel_gap"] <= 1e-6
-    ref = po.pins(w.dense_cost(), w.a, w.b, **kw)
+    ref = po.pins(w.dense_cost(), w.a, w.b, gamma=gamma, **kw)
     assert ref["rel_gap"] <= 1e-6
     tol = 1e-8 if prec == "fp64" else 1e-6
     assert abs(out["cost"] - ref["cost"]) / ref["cost"] <= tol
