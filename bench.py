@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=24, help="requests per stream (one step)")
     ap.add_argument("--rate", type=float, default=100.0,
                     help="Poisson arrival rate of the headline stream (req/s)")
-    ap.add_argument("--inflight", type=int, default=12, help="serving slots (max_inflight)")
+    ap.add_argument("--inflight", type=int, default=16, help="serving slots (max_inflight)")
     ap.add_argument("--sweep", default="0.5,1,2,4",
                     help="arrival rates of the saturation sweep ('' to skip)")
     ap.add_argument("--sweep-requests", type=int, default=16)
@@ -88,6 +88,12 @@ def parse():
                          "on an S x S grid (a warm-up solve first); the command the kernel "
                          "profiles under profiles/ capture")
     ap.add_argument("--fp64-seconds", type=float, default=120.0)
+    ap.add_argument("--grids", default="", metavar="S,...",
+                    help="instead of the contract line: one mixed solve of the bump-histogram "
+                         "instance on each S x S grid (cost generated on the fly), with the "
+                         "device memory the solve holds")
+    ap.add_argument("--grid-line", type=int, default=64, metavar="S",
+                    help="grid size of the default line's bump-histogram sub-object (0: skip)")
     a = ap.parse_args()
     if a.eta is None:
         a.eta = 2.5e-4 if a.workload == "strokes" else 1e-2
@@ -485,6 +491,12 @@ def run_ours_strokes(args):
     line["kernel_time_share"] = {k: round(v[0] / tot, 4) for k, v in prof.items() if v[1]}
     if args.hbm_roofline:
         line["hbm_roofline"] = lse_roofline(args, args.hbm_roofline)
+    if args.grid_line:
+        line["grid_histograms"] = grid_solve(args, args.grid_line)
+        line["grid_histograms"]["workload"] = (
+            "bump histograms (5-20 Gaussian bumps + 1e-6 floor) on a "
+            f"{args.grid_line} x {args.grid_line} grid, squared grid distance / max, "
+            "cost generated on the fly")
     if world == 1:
         done, dt, gmax = oracle_sample(args, args.cpu_seconds)
         line["cpu_baseline"] = {
@@ -616,6 +628,43 @@ def run_gmm4096(args):
           flush=True)
 
 
+def grid_solve(args, S, prec="mixed", K=None):
+    """One solve of the bump-histogram instance on an S x S grid (config 3's
+    recipe), certified gap target 1e-6.  Device memory: free memory before the
+    handle is created minus free memory after the solve (the handle keeps its
+    workspace until closed), so it covers everything the library holds."""
+    import torch
+    from paper_2502_03749_gb300 import pins, workloads as wl
+    w = wl.grid_instance(S, 0, eta=args.eta)
+    ref = pins.problem_from_workload(w)
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    cfg = solver_cfg(args, prec)
+    if K is not None:
+        cfg["K"] = K
+    h = pins.Pins(**cfg)
+    try:
+        t = time.perf_counter()
+        d = h.solve(ref, want_potentials=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t
+        free1, _ = torch.cuda.mem_get_info()
+    finally:
+        h.close()
+    return {"grid": S, "n": w.n, "entries_per_pass": float(w.n) * w.n, "prec": prec,
+            "seconds": t, "certified": bool(certified(d)), "rel_gap": d["rel_gap"],
+            "outer_iters": d["outer_iters"], "newton_iters": d["newton_iters"],
+            "cg_iters": d["cg_iters"], "status": d["status"],
+            "device_bytes": int(free0 - free1),
+            "dense_cost_bytes_if_stored": 4 * w.n * w.n}
+
+
+def run_grids(args):
+    for S in [int(x) for x in args.grids.split(",") if x]:
+        print(json.dumps(dict(mode="grid", eta=args.eta, gamma=args.gamma,
+                              **grid_solve(args, S, args.prec, args.K))), flush=True)
+
+
 def run_batch(args):
     """P stroke pairs solved by one pins_solve_batch call (instances run
     concurrently, batch_inflight at a time), certified to 1e-6."""
@@ -670,6 +719,9 @@ def main():
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.grids:
+        run_grids(args)
         return
     if args.impl == "reference":
         run_reference(args)

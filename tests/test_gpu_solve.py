@@ -274,15 +274,16 @@ def _hi_lp_opt(C, a, b):
     return float(res.fun)
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_points_instance_certified_to_1e6_at_eta_1e4(prec):
+def test_points_instance_certified_to_1e6_at_eta_1e4(prec, seed):
     """64 x 64 uniform points, random weights (the paper's smallest synthetic
     size), eta = 1e-4 (Table 3's most accurate setting): both paths stop on a
     certified relative gap <= 1e-6 within a few outer iterations (s/eta up to
     ~1e5).  FP64 follows the oracle's iterates (same outer count, cost and
     bounds within 1e-8); the mixed path solves the FP32-rounded cost and its
     error to that cost's LP optimum is at most the certified 1e-6."""
-    w = wl.small_points(0)
+    w = wl.small_points(seed)
     C = w.C if prec == "fp64" else w.C.astype(np.float32).astype(np.float64)
     kw = dict(eta=1e-4, tol_gap=1e-6, K=250)
     out = _solve(pins.make_problem("dense", w.a, w.b, C=C if prec == "fp64" else C.astype(np.float32)),
