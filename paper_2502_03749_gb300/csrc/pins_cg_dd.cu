@@ -55,6 +55,10 @@ namespace pins {
 // passes of the CG: the first, and restarts from x when the true residual at
 // the end of a pass is above twice the tolerance
 #define PINS_DDCG_PASSES 4
+// weight of an unknown against an entry in the work balance of the slices
+#ifndef PINS_DDCG_UW
+#define PINS_DDCG_UW 2
+#endif
 
 struct CGddArgs {
   int m, n;
@@ -72,6 +76,15 @@ struct CGddArgs {
   double rtol2; int max_iter; double* info;
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
 };
+
+// longest slice a CTA of a cluster of cs may own: twice the uniform share when
+// the shared memory holds it (room for balancing by work), else the share
+__host__ __device__ inline int ddcg_slice_cap(int N, int cs) {
+  const int Lu = (N + cs - 1) / cs;
+  if (cs == 1) return Lu;
+  const int L2 = 2 * Lu;
+  return ((size_t)PINS_DDCG_PER_UNKNOWN * ((L2 + 3) & ~3) + 16 <= PINS_DDCG_SMEM) ? L2 : Lu;
+}
 
 // LOCAL: a cluster of one CTA holds every unknown, so the SpMV reads m from its
 // own shared memory and nothing goes through the exchange buffer.
@@ -91,13 +104,47 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = a.m, N = a.m + a.n;
-  const int L = (N + CS - 1) / CS;
-  const int lo = rank * L;
-  const int nl = max(0, min(N, lo + L) - lo);
+  const int Kc = __ldg(a.indptr + m);
+  auto beg = [&](int t) -> int {
+    return (t < m) ? __ldg(a.indptr + t) : Kc + __ldg(a.colptr + t - m);
+  };
+  // Slices balanced by work: unknowns [b_k, b_{k+1}) go to CTA k, with b_k the
+  // first unknown whose cumulative cost (entries before it + PINS_DDCG_UW per
+  // unknown before it) reaches k/CS of the total, each slice at most Lcap long.
+  // Every CTA computes the same boundaries.
+  __shared__ int sbound[PINS_DDCG_MAX + 1];
+  const int Lcap = ddcg_slice_cap(N, CS);
+  if (warp == 0) {
+    const long long total = (long long)beg(N) + (long long)PINS_DDCG_UW * N;
+    int bk = 0;
+    if (lane > 0 && lane < CS) {
+      const long long target = (total * lane + CS - 1) / CS;
+      int lo_s = 0, hi_s = N;
+      while (lo_s < hi_s) {
+        const int mid = (lo_s + hi_s) >> 1;
+        if ((long long)beg(mid) + (long long)PINS_DDCG_UW * mid >= target) hi_s = mid; else lo_s = mid + 1;
+      }
+      bk = lo_s;
+    }
+    if (lane < CS) sbound[lane] = bk;
+    __syncwarp();
+    if (lane == 0) {
+      sbound[0] = 0;
+      for (int k = 1; k < CS; ++k) {
+        const int lower = max(sbound[k - 1], N - (CS - k) * Lcap);
+        const int upper = sbound[k - 1] + Lcap;
+        sbound[k] = min(max(sbound[k], lower), upper);
+      }
+      sbound[CS] = N;
+    }
+  }
+  __syncthreads();
+  const int lo = sbound[rank];
+  const int nl = sbound[rank + 1] - lo;
   // shared memory: the own slice (11 double-float arrays and 1 FP32 array of L4,
   // L4 + 4 row offsets), then, when the dynamic allocation has room, this CTA's
   // packed entries (target, value / eta, local row)
-  const int L4 = (L + 3) & ~3;
+  const int L4 = (Lcap + 3) & ~3;
   float2* xv = reinterpret_cast<float2*>(ddcg_smem);
   float2* rv = xv + L4;
   float2* uv = rv + L4;       // D^-1 r (recurrence)
@@ -114,10 +161,6 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   const size_t base_bytes = sizeof(float) * (size_t)(PINS_DDCG_PER_UNKNOWN / 4) * L4 + 16;
   float2* mg = reinterpret_cast<float2*>(a.ug);  // two buffers of N pairs
 
-  const int Kc = __ldg(a.indptr + m);
-  auto beg = [&](int t) -> int {
-    return (t < m) ? __ldg(a.indptr + t) : Kc + __ldg(a.colptr + t - m);
-  };
   const float2 ie = split_f64(a.inv_eta, 0);
   // the right-hand side: given, or the gradient (a - r; b - c) of the Newton step
   auto rhs_of = [&](int t) -> double {
@@ -207,6 +250,22 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     t0 = lo_s;
   }
   const bool starts_mid = (c0 < c1) && rb[t0] < c0;
+  // The slice structure is fixed for the launch: a row cut by this slice's
+  // start is its head (hrow), a row cut by its end its tail.  A tail is
+  // completed from the heads of the following slices up to run_end (empty
+  // slices, hrow = -2, contribute zero).
+  const int lastrow = (c0 < c1) ? erow[c1 - 1] : -1;
+  const bool single_run = (c0 < c1) && erow[c0] == lastrow;
+  const bool is_tail = (c0 < c1) && rb[lastrow + 1] > c1 && !(single_run && starts_mid);
+  hrow[tid] = (c0 < c1) ? (starts_mid ? erow[c0] : -1) : -2;
+  __syncthreads();
+  int run_end = tid;
+  if (is_tail)
+    for (int k = tid + 1; k < PINS_DDCG_TPB; ++k) {
+      if (hrow[k] == -2) continue;
+      if (hrow[k] != lastrow) break;
+      run_end = k;
+    }
 
   // od[t] = sum over the row/column entries of (S/eta) u, for the own unknowns.
   // Products first (independent), then a sum over runs of equal local row; a
@@ -254,17 +313,21 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
       else if (rb[cur + 1] > c1) { tailrow = cur; tailv = acc; }
       else od[cur] = acc;
     }
-    hrow[tid] = (c0 < c1) ? headrow : -2;           // -2: empty slice, skipped below
-    hval[tid] = headv;
+    (void)headrow;
+    hval[tid] = headv;                              // zero for an empty slice or no head
     __syncthreads();
     if (tailrow >= 0) {
-      float2 s = tailv;
-      for (int k = tid + 1; k < PINS_DDCG_TPB; ++k) {
-        if (hrow[k] == -2) continue;
-        if (hrow[k] != tailrow) break;
-        s = ddv_add(s, hval[k]);
+      // heads of the following slices, four independent partial sums
+      float2 s0 = tailv, s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+      int k = tid + 1;
+      for (; k + 3 <= run_end; k += 4) {
+        s0 = ddv_add(s0, hval[k]);
+        s1 = ddv_add(s1, hval[k + 1]);
+        s2 = ddv_add(s2, hval[k + 2]);
+        s3 = ddv_add(s3, hval[k + 3]);
       }
-      od[tailrow] = s;
+      for (; k <= run_end; ++k) s0 = ddv_add(s0, hval[k]);
+      od[tailrow] = ddv_add(ddv_add(s0, s1), ddv_add(s2, s3));
     }
     __syncthreads();
   };
@@ -519,7 +582,7 @@ static int ddcg_max_cluster() {
 }
 
 size_t ddcg_smem_bytes(int N, int cs) {
-  const int L4 = (((N + cs - 1) / cs) + 3) & ~3;
+  const int L4 = (ddcg_slice_cap(N, cs) + 3) & ~3;
   return (size_t)PINS_DDCG_PER_UNKNOWN * L4 + 16;
 }
 
@@ -543,7 +606,7 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
   *used = false;
   const int N = m + n;
   const int CS = ddcg_cluster_for(N, ddcg_max_cluster());
-  const int L = (N + CS - 1) / CS;
+  const int L = ddcg_slice_cap(N, CS);
   if (ddcg_smem_bytes(N, CS) > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
   const size_t smem = PINS_DDCG_SMEM;   // the rest holds a copy of u and the entries when they fit
   CGddArgs a;

@@ -74,6 +74,7 @@ struct SparseWS {
   int* colptr; int* rowidx; double* cdata;    // CSC: n+1, cap, cap
   int* trow; double* tval;       // CSC placement before the per-column sort: cap, cap
   int* tcol; double* tcval;      // CSR placement before the per-row sort (one-pass selection)
+  int* longseg; int* nlong;      // segments longer than a warp sorts: m + n tags, count
 };
 void build_csc_from_csr(const int* indptr, const int* indices, const double* data, int m, int n,
                         int nnz, const SparseWS& sw, cudaStream_t st);

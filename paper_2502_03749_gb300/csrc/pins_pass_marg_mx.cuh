@@ -82,19 +82,39 @@ k_marg_mx(PassArgs p, MergeWS ws, TrialArgs tr, double* r_out, double* c_out, do
           bool keep = false;
           float zh = 0.f, zl = 0.f;
           if (j < j1) {
-            float wh, wl;
-            dd_w(sB[j - j0], c[q], kh, kl, wh, wl);
-            dd_z(A, wh, wl, zh, zl);
-            float zf = __fadd_rn(zh, zl);
+            // FP32 estimate of z from the leading parts; its error is below a
+            // few ulps of the largest term, so with the bound `lim` an entry
+            // estimated below it is below e^-87 at the evaluated point(s) and
+            // skips the double-float exponent: the kept set is exactly that of
+            // the exact test
+            const float2 Bj = sB[j - j0];
+            const float kc = __fmul_rn(kh, c[q]);
+            const float est = __fadd_rn(A.x, __fsub_rn(Bj.x, kc));
+            const float lim = __fmaf_rn(-2.5e-7f, fabsf(A.x) + fabsf(Bj.x) + kc, -88.0f);
+            float zf = est;
+            float t1 = 0.f;
             if constexpr (TRIAL) {
-              // FP32 estimate of the trial point's exponent: it only places the
-              // e^-87 skip threshold and the sparsify window; the listed
-              // entries get z + t in double-float below
-              const float z1 = __fadd_rn(zf, __fadd_rn(Pt.x, sQ[j - j0].x));
-              keep = (zf > -87.0f) || (z1 > -87.0f);
-              zf = z1;
+              t1 = __fadd_rn(Pt.x, sQ[j - j0].x);
+              keep = (est > lim) || (__fadd_rn(est, t1) > lim - 2.5e-7f * fabsf(t1));
+              zf = __fadd_rn(est, t1);
             } else {
-              keep = zf > -87.0f;
+              keep = est > lim;
+            }
+            if (keep) {
+              float wh, wl;
+              dd_w(Bj, c[q], kh, kl, wh, wl);
+              dd_z(A, wh, wl, zh, zl);
+              zf = __fadd_rn(zh, zl);
+              if constexpr (TRIAL) {
+                // FP32 estimate of the trial point's exponent: it only places the
+                // e^-87 skip threshold and the sparsify window; the listed
+                // entries get z + t in double-float below
+                const float z1 = __fadd_rn(zf, t1);
+                keep = (zf > -87.0f) || (z1 > -87.0f);
+                zf = z1;
+              } else {
+                keep = zf > -87.0f;
+              }
             }
             zmaxf = fmaxf(zmaxf, zf);
           }

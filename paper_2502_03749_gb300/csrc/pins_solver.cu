@@ -102,6 +102,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.sw.cdata = cv.take<double>(kcap);
   w.sw.trow = cv.take<int>(kcap); w.sw.tval = cv.take<double>(kcap);
   w.sw.tcol = cv.take<int>(kcap); w.sw.tcval = cv.take<double>(kcap);
+  w.sw.longseg = cv.take<int>(N); w.sw.nlong = cv.take<int>(1);
   w.fkey = cv.take<float>(PINS_FAST_CAP); w.fij = cv.take<unsigned long long>(PINS_FAST_CAP);
   w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
   w.ent_row = cv.take<int>(2 * (size_t)kcap);
@@ -539,7 +540,7 @@ pins_status Solver::sparsify(double s, int keep, double zmax, int* nnz_out, bool
     prof_begin(PC_CSC);
     build_csc_from_csr(ws_.sw.indptr, ws_.sw.indices, ws_.sw.data, m_, n_, keep, ws_.sw, stream_);
     prof_end();
-    launches_ += 4;
+    launches_ += 5;
   }
   *nnz_out = keep;
   return check("csr");
@@ -558,7 +559,7 @@ void Solver::sparsify_fast(double s, int keep, float tau_guess) {
   prof_begin(PC_WRITE);
   build_sparse_from_candidates(fs, ws_.fkey, ws_.fij, m_, n_, keep, ws_.sw, stream_);
   prof_end();
-  launches_ += 6;
+  launches_ += 7;
 }
 
 pins_status Solver::certificate(double s, double zmax) {
@@ -936,7 +937,7 @@ pins_status Solver::step_cg(int m, int n, double eta, const double* r, const dou
   cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // index-check flag
   cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, rhs, d, rtol,
                           max_iter, info, nullptr, nullptr);
-  launches_ += 5;
+  launches_ += 6;
   if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); return PINS_ERR_CUDA; }
   return sync("step_cg");
 }

@@ -126,31 +126,83 @@ __device__ __forceinline__ void warp_sort_segment(int b, int len, const int* tro
   }
 }
 // one warp sorts segment j of (trow, tval) by row into (rowidx, cdata); fill[j] = 0.
-// Keys are unique within a segment, so the order is deterministic.
+// Keys are unique within a segment, so the order is deterministic.  Segments
+// longer than 128 entries are appended to a list (as `tag`) for k_long_segsort.
 __device__ __forceinline__ void warp_seg_sort(int j, const int* ptr, int* fill, const int* trow,
-                                              const double* tval, int* rowidx, double* cdata) {
+                                              const double* tval, int* rowidx, double* cdata,
+                                              int tag, int* longseg, int* nlong) {
   const int lane = threadIdx.x & 31;
   const int b = ptr[j], len = ptr[j + 1] - b;
   if (lane == 0) fill[j] = 0;
   if (len <= 32) warp_sort_segment<1>(b, len, trow, tval, rowidx, cdata);
   else if (len <= 64) warp_sort_segment<2>(b, len, trow, tval, rowidx, cdata);
   else if (len <= 128) warp_sort_segment<4>(b, len, trow, tval, rowidx, cdata);
-  else {
-    // long segment: each entry's rank is the number of smaller rows
-    for (int q = lane; q < len; q += 32) {
-      const int r = trow[b + q];
-      int rank = 0;
-      for (int t = 0; t < len; ++t) rank += (trow[b + t] < r) ? 1 : 0;
-      rowidx[b + rank] = r;
-      cdata[b + rank] = tval[b + q];
+  else if (lane == 0) longseg[atomicAdd(nlong, 1)] = tag;
+}
+
+// Long segments, one CTA each: a bitonic sort in shared memory for up to
+// PINS_LONGSEG entries, rank counting above that.  tag < m: row tag of the CSR
+// (by column); tag >= m: column tag - m of the CSC (by row).
+#define PINS_LONGSEG 4096
+__global__ void __launch_bounds__(1024)
+k_long_segsort(const int* nlong, const int* longseg, int m, const int* indptr, const int* tcol,
+               const double* tcval, int* indices, double* data, const int* colptr,
+               const int* trow, const double* tval, int* rowidx, double* cdata) {
+  extern __shared__ unsigned char lsm[];
+  double* sv = reinterpret_cast<double*>(lsm);
+  int* sk = reinterpret_cast<int*>(sv + PINS_LONGSEG);
+  const int cnt = *nlong;
+  for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+    const int tag = longseg[q];
+    const bool row = tag < m;
+    const int* ptr = row ? indptr : colptr;
+    const int id = row ? tag : tag - m;
+    const int* tk = row ? tcol : trow;
+    const double* tv = row ? tcval : tval;
+    int* ok = row ? indices : rowidx;
+    double* ov = row ? data : cdata;
+    const int b = ptr[id], len = ptr[id + 1] - b;
+    if (len <= PINS_LONGSEG) {
+      int P2 = 1;
+      while (P2 < len) P2 <<= 1;
+      for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+        sk[t] = (t < len) ? tk[b + t] : 0x7fffffff;
+        sv[t] = (t < len) ? tv[b + t] : 0.0;
+      }
+      __syncthreads();
+      for (int k = 2; k <= P2; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+          for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+            const int l = t ^ jj;
+            if (l > t) {
+              const bool up = (t & k) == 0;
+              if (up ? sk[t] > sk[l] : sk[t] < sk[l]) {
+                const int x = sk[t]; sk[t] = sk[l]; sk[l] = x;
+                const double y = sv[t]; sv[t] = sv[l]; sv[l] = y;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      for (int t = threadIdx.x; t < len; t += blockDim.x) { ok[b + t] = sk[t]; ov[b + t] = sv[t]; }
+      __syncthreads();
+    } else {
+      for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        const int r = tk[b + t];
+        int rank = 0;
+        for (int u = 0; u < len; ++u) rank += (tk[b + u] < r) ? 1 : 0;
+        ok[b + rank] = r;
+        ov[b + rank] = tv[b + t];
+      }
     }
   }
 }
-__global__ void k_csc_segsort(const int* colptr, int n, int* fill, const int* trow,
-                              const double* tval, int* rowidx, double* cdata) {
+__global__ void k_csc_segsort(const int* colptr, int m, int n, int* fill, const int* trow,
+                              const double* tval, int* rowidx, double* cdata, int* longseg,
+                              int* nlong) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < n; j += nw)
-    warp_seg_sort(j, colptr, fill, trow, tval, rowidx, cdata);
+    warp_seg_sort(j, colptr, fill, trow, tval, rowidx, cdata, m + j, longseg, nlong);
 }
 
 // ------------------------------------------------------------------------- //
@@ -231,13 +283,25 @@ __global__ void k_fast_place(const FastSelState* fs, const float* ckey,
 __global__ void k_fast_segsort(const FastSelState* fs, int m, int n, const int* indptr,
                                int* rowfill, const int* tcol, const double* tcval, int* indices,
                                double* data, const int* colptr, int* colfill, const int* trow,
-                               const double* tval, int* rowidx, double* cdata) {
+                               const double* tval, int* rowidx, double* cdata, int* longseg,
+                               int* nlong) {
   if (fs->fail) return;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < m + n; s += nw) {
-    if (s < m) warp_seg_sort(s, indptr, rowfill, tcol, tcval, indices, data);
-    else warp_seg_sort(s - m, colptr, colfill, trow, tval, rowidx, cdata);
+    if (s < m) warp_seg_sort(s, indptr, rowfill, tcol, tcval, indices, data, s, longseg, nlong);
+    else warp_seg_sort(s - m, colptr, colfill, trow, tval, rowidx, cdata, s, longseg, nlong);
   }
+}
+static void launch_long_segsort(int m, const SparseWS& sw, cudaStream_t st) {
+  static const bool configured = [] {
+    cudaFuncSetAttribute(k_long_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(PINS_LONGSEG * (sizeof(double) + sizeof(int))));
+    return true;
+  }();
+  (void)configured;
+  k_long_segsort<<<152, 1024, PINS_LONGSEG * (sizeof(double) + sizeof(int)), st>>>(
+      sw.nlong, sw.longseg, m, sw.indptr, sw.tcol, sw.tcval, sw.indices, sw.data, sw.colptr,
+      sw.trow, sw.tval, sw.rowidx, sw.cdata);
 }
 
 void build_sparse_from_candidates(const FastSelState* fs, const float* ckey,
@@ -249,9 +313,11 @@ void build_sparse_from_candidates(const FastSelState* fs, const float* ckey,
   k_fast_place<<<cb, 256, 0, st>>>(fs, ckey, cij, sw.indptr, sw.rowcnt, sw.tcol, sw.tcval,
                                    sw.colptr, sw.colcnt, sw.trow, sw.tval);
   const int sb = std::max(1, std::min((m + n + 7) / 8, 2368));
+  cudaMemsetAsync(sw.nlong, 0, sizeof(int), st);
   k_fast_segsort<<<sb, 256, 0, st>>>(fs, m, n, sw.indptr, sw.rowcnt, sw.tcol, sw.tcval,
                                      sw.indices, sw.data, sw.colptr, sw.colcnt, sw.trow, sw.tval,
-                                     sw.rowidx, sw.cdata);
+                                     sw.rowidx, sw.cdata, sw.longseg, sw.nlong);
+  launch_long_segsort(m, sw, st);
   (void)keep;
 }
 
@@ -264,8 +330,10 @@ void build_csc_from_csr(const int* indptr, const int* indices, const double* dat
   k_csc_place<<<pb, 256, 0, st>>>(indptr, indices, data, m, sw.colptr, sw.colcnt, sw.trow,
                                   sw.tval);
   const int sb = std::max(1, std::min((n + 7) / 8, 2368));
-  k_csc_segsort<<<sb, 256, 0, st>>>(sw.colptr, n, sw.colcnt, sw.trow, sw.tval, sw.rowidx,
-                                    sw.cdata);
+  cudaMemsetAsync(sw.nlong, 0, sizeof(int), st);
+  k_csc_segsort<<<sb, 256, 0, st>>>(sw.colptr, m, n, sw.colcnt, sw.trow, sw.tval, sw.rowidx,
+                                    sw.cdata, sw.longseg, sw.nlong);
+  launch_long_segsort(m, sw, st);
 }
 
 // ------------------------------------------------------------------------- //
