@@ -107,14 +107,16 @@ __device__ __forceinline__ float2 ddv_scale(float f, float2 v) {
   return make_float2(h, l);
 }
 __device__ __forceinline__ float2 ddv_neg(float2 a) { return make_float2(-a.x, -a.y); }
-// a / b for double-float a, b: the FP32 quotient of the leading parts corrected
-// by the remainder a - q b (formed exactly by TwoProduct), normalised
+// a / b for double-float a, b: an FP32 quotient of the leading parts corrected
+// by the remainder a - q b (formed exactly by TwoProduct), normalised.  The
+// correction absorbs the error of the fast reciprocal quotient.
 __device__ __forceinline__ float2 ddv_div(float2 a, float2 b) {
-  const float q1 = __fdiv_rn(a.x, b.x);
+  const float ib = __frcp_rn(b.x);
+  const float q1 = __fmul_rn(a.x, ib);
   float p, e; two_prod(q1, b.x, p, e);
   e = __fmaf_rn(q1, b.y, e);
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), e), a.y);
-  const float q2 = __fdiv_rn(r, b.x);
+  const float q2 = __fmul_rn(r, ib);
   float h, l; fast_two_sum(q1, q2, h, l);
   return make_float2(h, l);
 }
