@@ -185,8 +185,11 @@ SMS, FP32_LANES, MUFU_PER_SM, SM_GHZ = 152, 128, 16, 2.07
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_GHZ * 1e9 / 1e12     # FMA = 2 flops
 EX2_PEAK_GPS = SMS * MUFU_PER_SM * SM_GHZ                          # G ex2 per second
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
-# the class's kernel (profiles/); None once the kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {}
+# the class's kernel on the roofline's workload (profiles/); remove an entry
+# once its kernel changes after the capture.
+NCU_TRAFFIC_BYTES = {
+    "cg": 664576 + 1024,     # k_pcg_dd, 64 x 64 stroke pair (profiles/k_pcg_dd_stroke64.md)
+}
 
 
 def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, streamed):
@@ -209,7 +212,8 @@ def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, streamed):
         per_launch = (4.0 * nnz + 14.0 * (m + n)) * iters
         achieved = per_launch / t / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": NCU_TRAFFIC_BYTES.get(dom),
                 "peak_source": "derived: FP32 units x clock (152 x 128 x 2 x 2.07 GHz)",
                 "work": "4 nnz + 14 (m + n) flops per CG iteration (the method's own work)",
                 "avg_launch_us": t * 1e6, "launches": cnt, "iters_per_launch": iters,
