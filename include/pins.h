@@ -72,8 +72,8 @@ typedef enum {
   /* m x n passes on the FP32 units: the Sinkhorn warm-up uses FP32 exp on a
    * double-float (compensated) exponent; the gradient, line-search, stopping and
    * certificate passes use a double-float table-driven exp (~1e-13 relative).
-   * The CG keeps its vectors, matrix-vector product and inner products in
-   * double-float (about 48 significand bits) and checks the true residual
+   * The CG keeps its vectors, matrix-vector product, inner products and step
+   * lengths in double-float (about 48 significand bits) and checks the true residual
    * rhs - M x when its recurrence meets the tolerance.  Potentials, the outer
    * update and the stopping decisions stay FP64.  A dense FP64 cost is rounded
    * to FP32 once. */
@@ -242,8 +242,10 @@ pins_status pins_step_sparsify(pins_handle* h, const pins_problem* p, double s,
  * Eq. eq:eppa-hess).  S is CSR (indptr m+1, indices/data nnz).  rhs, d: m + n
  * device doubles.  info (device, 2 doubles) = {iterations, relative residual}.
  * On a PINS_PREC_FP64 handle every operation is FP64.  On a PINS_PREC_MIXED
- * handle the vectors, the matrix-vector product and the inner products are
- * kept in double-float (FP32 pairs, ~48 significand bits); when the recurrence
+ * handle the vectors, the matrix-vector product, the inner products and the
+ * step lengths are kept in double-float (FP32 pairs, ~48 significand bits), in
+ * the single-reduction ordering that gives the textbook PCG's iterates in exact
+ * arithmetic (its iteration count within a few per cent); when the recurrence
  * residual meets rtol, the true residual rhs - M d is formed and, if it is
  * above 2 rtol ||rhs||, the iteration restarts from d (at most three times).
  * info[1] is then the last measured ||r|| / ||rhs||. */

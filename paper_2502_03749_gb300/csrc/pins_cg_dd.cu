@@ -7,29 +7,35 @@
 // FP64 latency sets its length.  Every vector, the matrix-vector product
 // (diagonal and S entries scaled by 1/eta) and the three inner products per
 // iteration (r.u, w.u, r.r) keep ~48 significand bits; the step lengths alpha,
-// beta are formed in FP64 from them and applied as FP32 scalars (the same value
-// in every recurrence, so the recurrences stay consistent).  FP32 inner
-// products, measured on the Newton systems of 64 x 64 grid problems, doubled
-// the iteration count against FP64 CG and let the recurrence residual drift
-// from the true one by two orders of magnitude.  The preconditioner is D^-1
-// with D^-1 rounded to FP32 (a fixed diagonal).  rhs is scaled by a power of
-// two (exact) so that its largest entry is in [1, 2); x is scaled back at the
-// end.
+// beta are formed and applied in double-float (the same value in every
+// recurrence, so the recurrences stay consistent).  FP32
+// inner products, measured on the Newton systems of 64 x 64 grid problems,
+// doubled the iteration count against FP64 CG and let the recurrence residual
+// drift from the true one by two orders of magnitude.  The preconditioner is
+// D^-1 with D^-1 rounded to FP32 (a fixed diagonal).  rhs is scaled by a power
+// of two (exact) so that its largest entry is in [1, 2); x is scaled back at
+// the end.
 //
-// Ordering: the pipelined PCG of Ghysels & Vanroose (Parallel Computing 40,
-// 2014), which puts the one global reduction of an iteration and its
-// matrix-vector product behind the same synchronisation:
-//   (r.u, w.u, r.r) partials, m = D^-1 w        -> publish    [cluster barrier]
+// Ordering: the single-reduction PCG of Chronopoulos & Gear (J. Comput. Appl.
+// Math. 25, 1989), as in the FP64 cluster CG:
+//   u = D^-1 r published                                  [cluster barrier]
+//   w = M u;  (r.u, w.u, r.r) partials published          [cluster barrier]
 //   gamma, delta, rr (every CTA, same order);  stop if rr <= rtol^2 rr_0
-//   beta = gamma/gamma', alpha = gamma/(delta - beta gamma/alpha');  n = M m
-//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
-//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.
+//   beta = gamma/gamma', alpha = gamma/(delta - beta gamma/alpha')
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s
 // In exact arithmetic these are the iterates, and the iteration count, of the
-// textbook Jacobi PCG with the same stopping rule.  The m slices go through L2
-// (two alternating buffers, so one barrier per iteration suffices), the block
-// partials through distributed shared memory (two alternating slot sets).  A
-// system small enough for one CTA runs in a cluster of one, which reads m from
-// its own shared memory.
+// textbook Jacobi PCG with the same stopping rule.  The pipelined ordering of
+// Ghysels & Vanroose (Parallel Computing 40, 2014) saves the second barrier by
+// carrying M u, M D^-1 w and two more vectors as recurrences; on the Newton
+// systems of grid problems (Jacobi-preconditioned condition numbers that take
+// textbook PCG thousands of iterations) those recurrences drift: in FP64 the
+// pipelined iteration stalls where the textbook one converges, and here it
+// needed 2.6x the textbook iterations with restarts.  The single-reduction
+// form follows the textbook count within a few per cent at this precision.
+// The u slices go through L2 (one buffer: its reads and writes are separated by
+// a barrier each way), the block partials through distributed shared memory
+// (two alternating slot sets).  A system small enough for one CTA runs in a
+// cluster of one, which reads u from its own shared memory.
 // Every CTA sums the block partials in the same order and takes the same
 // decisions, so results are reproducible run to run.
 #include <cooperative_groups.h>
@@ -50,8 +56,8 @@ namespace pins {
 // (4.1 us) beat 4 (4.5 us) and 16 (4.5 us); on 8192, 16 CTAs (5.9 us) beat 8 (7.1 us).
 #define PINS_DDCG_LOCAL_MAX 512
 #define PINS_DDCG_SLICE 256
-// shared bytes per unknown: x, r, u, w, z, q, s, p, m, diag, od (11 x 8) + D^-1 (4) + row begin (4)
-#define PINS_DDCG_PER_UNKNOWN 96
+// shared bytes per unknown: x, r, u, w, s, p, diag, od (8 x 8) + D^-1 (4) + row begin (4)
+#define PINS_DDCG_PER_UNKNOWN 72
 // passes of the CG: the first, and restarts from x when the true residual at
 // the end of a pass is above twice the tolerance
 #define PINS_DDCG_PASSES 4
@@ -71,7 +77,7 @@ struct CGddArgs {
   double* dots;                    // if not NULL: <rhs, x> and <ab, x> (FP64, fixed order)
   int* ent_tgt; float2* ent_val;   // scratch: one slot per entry of the CSR + CSC entry space
   int* ent_row;
-  float* ug;                       // u of every unknown (N floats), the exchange buffer
+  float* ug;                       // exchange buffers: u, then x (2 N double-float pairs)
   size_t smem_bytes;               // dynamic shared memory of the launch
   double rtol2; int max_iter; double* info;
   int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
@@ -141,25 +147,23 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   __syncthreads();
   const int lo = sbound[rank];
   const int nl = sbound[rank + 1] - lo;
-  // shared memory: the own slice (11 double-float arrays and 1 FP32 array of L4,
+  // shared memory: the own slice (8 double-float arrays and 1 FP32 array of L4,
   // L4 + 4 row offsets), then, when the dynamic allocation has room, this CTA's
   // packed entries (target, value / eta, local row)
   const int L4 = (Lcap + 3) & ~3;
   float2* xv = reinterpret_cast<float2*>(ddcg_smem);
   float2* rv = xv + L4;
-  float2* uv = rv + L4;       // D^-1 r (recurrence)
+  float2* uv = rv + L4;       // D^-1 r (published in the exchange buffer)
   float2* wv = uv + L4;       // M u
-  float2* zv = wv + L4;
-  float2* qv = zv + L4;
-  float2* sv = qv + L4;
+  float2* sv = wv + L4;       // M p (recurrence)
   float2* pv = sv + L4;
-  float2* mv = pv + L4;       // D^-1 w (published in the exchange buffer)
-  float2* dg = mv + L4;       // diag / eta
-  float2* od = dg + L4;       // off-diagonal part of M m (zeroed after use)
+  float2* dg = pv + L4;       // diag / eta
+  float2* od = dg + L4;       // off-diagonal part of M u (zeroed after use)
   float* dinv = reinterpret_cast<float*>(od + L4);
   int* rb = reinterpret_cast<int*>(dinv + L4);   // nl + 1 entry offsets (relative to E0)
   const size_t base_bytes = sizeof(float) * (size_t)(PINS_DDCG_PER_UNKNOWN / 4) * L4 + 16;
-  float2* mg = reinterpret_cast<float2*>(a.ug);  // two buffers of N pairs
+  float2* ug0 = reinterpret_cast<float2*>(a.ug);  // u of every unknown
+  float2* ug1 = ug0 + N;                          // x of every unknown (true residual)
 
   const float2 ie = split_f64(a.inv_eta, 0);
   // the right-hand side: given, or the gradient (a - r; b - c) of the Newton step
@@ -202,8 +206,6 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     dg[k] = dd_;
     dinv[k] = __frcp_rn(dd_.x);
     xv[k] = make_float2(0.f, 0.f);
-    zv[k] = make_float2(0.f, 0.f);
-    qv[k] = make_float2(0.f, 0.f);
     sv[k] = make_float2(0.f, 0.f);
     pv[k] = make_float2(0.f, 0.f);
     od[k] = make_float2(0.f, 0.f);
@@ -371,9 +373,6 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     t0r = q0; t1r = q1; t2r = q2;
   };
 
-  // (r.u, w.u, r.r) partials (double-float products and sums) and m = D^-1 w of
-  // the own unknown k, m published in exchange buffer b (the next iteration's
-  // phase A, fused into the vector updates)
   // acc += x y for double-float x, y, accumulated unnormalised (hi by TwoSum,
   // every lower-order term into lo); normalised once in the reductions below
   auto acc2 = [](float2& acc, float2 x, float2 y) {
@@ -382,133 +381,102 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     float sh, st; two_sum(acc.x, p, sh, st);
     acc.x = sh; acc.y = __fadd_rn(acc.y, __fadd_rn(st, e));
   };
-  auto phase_a = [&](int k, float2 w, float2 rk, float2 uk, int b, float2& lg, float2& ld,
-                     float2& lrr) {
-    acc2(lg, rk, uk);
-    acc2(ld, w, uk);
-    acc2(lrr, rk, rk);
-    const float2 mk = ddv_scale(dinv[k], w);
-    mv[k] = mk;
-    if (!LOCAL) __stcg(mg + (size_t)b * N + lo + k, mk);
+  // a barrier over the cluster; a cluster of one needs only its block's
+  auto csync = [&]() {
+    if (LOCAL) __syncthreads(); else cluster.sync();
   };
+  const float2 zero = make_float2(0.f, 0.f);
 
-  // Passes: pipelined PCG from (x, r) until the recurrence residual meets the
-  // tolerance; then the true residual rhs - M x is formed (one more exchange and
-  // SpMV).  If it is above twice the tolerance -- the recurrences of a long run
-  // can drift from it -- the next pass restarts from x with r = rhs - M x.
-  // the scalar recurrences run in double-float on the FP32 units: FP64 on this
-  // GPU issues at ~1/64 of the FP32 rate and every thread forms the scalars
+  // Passes: PCG from (x, r) until the recurrence residual meets the tolerance;
+  // then the true residual rhs - M x is formed (one more exchange and SpMV).  If
+  // it is above twice the tolerance -- the recurrences of a long run can drift
+  // from it -- the next pass restarts from x with r = rhs - M x.  The scalar
+  // recurrences run in double-float on the FP32 units: FP64 on this GPU issues
+  // at ~1/64 of the FP32 rate and every thread forms the scalars.
   const float tol2 = (float)a.rtol2;
-  float2 bb = make_float2(0.f, 0.f), rr = bb;
-  int it = 0, buf = 0;
+  float2 bb = zero, rr = zero;
+  int it = 0, sb = 0;                               // sb: slot set of the next publish
   bool conv = false;
   for (int pass = 0; pass < PINS_DDCG_PASSES; ++pass) {
-    // u0 = D^-1 r0 published in exchange buffer 1 for w0 = M u0; z, q, s, p = 0
+    // u0 = D^-1 r0 published; p = s = 0 (the first step takes beta = 0)
     for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
       const float2 u0 = ddv_scale(dinv[k], rv[k]);
       uv[k] = u0;
-      mv[k] = u0;
-      zv[k] = make_float2(0.f, 0.f);
-      qv[k] = make_float2(0.f, 0.f);
-      sv[k] = make_float2(0.f, 0.f);
-      pv[k] = make_float2(0.f, 0.f);
-      if (!LOCAL) __stcg(mg + N + lo + k, u0);
-    }
-    cluster.sync();                                 // every u0 slice published
-    spmv(mg + N, mv);
-    buf = 0;
-    float2 lg = make_float2(0.f, 0.f), ld = lg, lrr = lg;
-    for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
-      const float2 w = ddv_add(ddv_mul(dg[k], mv[k]), od[k]);
-      wv[k] = w;
-      od[k] = make_float2(0.f, 0.f);
-      phase_a(k, w, rv[k], uv[k], buf, lg, ld, lrr);
+      sv[k] = zero;
+      pv[k] = zero;
+      if (!LOCAL) __stcg(ug0 + lo + k, u0);
     }
     float2 gam_prev = make_float2(1.f, 0.f), alpha_prev = gam_prev;
     int itr = 0;
     conv = false;
     while (true) {
-      publish3(lg, ld, lrr, buf);
-      cluster.sync();                               // m slices and partials published
-      // phase B: scalars (identical in every CTA), then n = M m
+      csync();                                      // every u slice published
+      spmv(ug0, uv);
+      // w = M u of the own unknowns and the (r.u, w.u, r.r) partials
+      float2 lg = zero, ld = zero, lrr = zero;
+      for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+        const float2 uk = uv[k], rk = rv[k];
+        const float2 w = ddv_add(ddv_mul(dg[k], uk), od[k]);
+        wv[k] = w;
+        od[k] = zero;
+        acc2(lg, rk, uk);
+        acc2(ld, w, uk);
+        acc2(lrr, rk, rk);
+      }
+      publish3(lg, ld, lrr, sb);
+      csync();                                      // partials published
+      // scalars (identical in every CTA)
       float2 gam, dlt;
-      gather3(buf, gam, dlt, rr);
+      gather3(sb, gam, dlt, rr);
+      sb ^= 1;
       if (pass == 0 && itr == 0) bb = rr;
       if (!(bb.x > 0.f)) break;
       if (!(rr.x > tol2 * bb.x)) { conv = true; break; }
       if (!(rr.x == rr.x) || it >= a.max_iter) break;   // NaN or the cap stops
       // beta = gam / gam', alpha = gam / (dlt - beta gam / alpha'); the
       // difference can cancel, so it is formed in double-float
-      const float2 beta = (itr == 0) ? make_float2(0.f, 0.f) : ddv_div(gam, gam_prev);
+      const float2 beta = (itr == 0) ? zero : ddv_div(gam, gam_prev);
       const float2 den = (itr == 0) ? dlt
                                     : ddv_add(dlt, ddv_neg(ddv_div(ddv_mul(beta, gam), alpha_prev)));
       const float2 alpha = ddv_div(gam, den);
-      const float bf = beta.x + beta.y, af = alpha.x + alpha.y;
-      spmv(mg + (size_t)buf * N, mv);
-      // two unknowns per step, loads first, so their dependency chains overlap;
-      // phase A of the next iteration follows each unknown's update (the same
-      // summation order as a separate pass over k = tid, tid + TPB, ...)
-      const int nb = buf ^ 1;
-      lg = make_float2(0.f, 0.f); ld = lg; lrr = lg;
-      for (int k = tid; k < nl; k += 2 * PINS_DDCG_TPB) {
-        const int k2 = k + PINS_DDCG_TPB;
-        const bool two = k2 < nl;
-        const int kk[2] = {k, two ? k2 : k};
-        float2 n0[2], z0[2], q0[2], s0[2], p0[2], x0[2], r0[2], u0[2], w0[2], m0[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int t = kk[h];
-          n0[h] = ddv_add(ddv_mul(dg[t], mv[t]), od[t]);
-          z0[h] = zv[t]; q0[h] = qv[t]; s0[h] = sv[t]; p0[h] = pv[t];
-          x0[h] = xv[t]; r0[h] = rv[t]; u0[h] = uv[t]; w0[h] = wv[t]; m0[h] = mv[t];
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          z0[h] = ddv_axpy(bf, z0[h], n0[h]);
-          q0[h] = ddv_axpy(bf, q0[h], m0[h]);
-          s0[h] = ddv_axpy(bf, s0[h], w0[h]);
-          p0[h] = ddv_axpy(bf, p0[h], u0[h]);
-          x0[h] = ddv_axpy(af, p0[h], x0[h]);
-          r0[h] = ddv_axpy(-af, s0[h], r0[h]);
-          u0[h] = ddv_axpy(-af, q0[h], u0[h]);
-          w0[h] = ddv_axpy(-af, z0[h], w0[h]);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !two) break;
-          const int t = kk[h];
-          od[t] = make_float2(0.f, 0.f);
-          zv[t] = z0[h]; qv[t] = q0[h]; sv[t] = s0[h]; pv[t] = p0[h];
-          xv[t] = x0[h]; rv[t] = r0[h]; uv[t] = u0[h]; wv[t] = w0[h];
-          phase_a(t, w0[h], r0[h], u0[h], nb, lg, ld, lrr);
-        }
+      const float2 nalpha = ddv_neg(alpha);
+      // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
+      // with double-float step lengths: rounding them to FP32 (relative 2^-24
+      // per step) costs conjugacy fast enough that these systems stall
+      for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
+        const float2 pk = ddv_axpy2(beta, pv[k], uv[k]);
+        const float2 sk = ddv_axpy2(beta, sv[k], wv[k]);
+        const float2 xk = ddv_axpy2(alpha, pk, xv[k]);
+        const float2 rk = ddv_axpy2(nalpha, sk, rv[k]);
+        const float2 uk = ddv_scale(dinv[k], rk);
+        pv[k] = pk; sv[k] = sk; xv[k] = xk; rv[k] = rk; uv[k] = uk;
+        if (!LOCAL) __stcg(ug0 + lo + k, uk);
       }
       gam_prev = gam;
       alpha_prev = alpha;
       ++it;
       ++itr;
-      buf = nb;
     }
     if (!conv || pass + 1 == PINS_DDCG_PASSES) break;
-    // true residual t = rhs - M x: x goes through the exchange buffer nobody reads
-    // now (buffer buf ^ 1 was last read before the barrier that ended the loop)
-    const int xb = buf ^ 1;
+    // true residual t = rhs - M x: x goes through its own exchange buffer, last
+    // read before the barrier of the previous pass's check
     if (!LOCAL)
-      for (int k = tid; k < nl; k += PINS_DDCG_TPB) __stcg(mg + (size_t)xb * N + lo + k, xv[k]);
-    cluster.sync();                                 // x slices published, slots gathered
-    spmv(mg + (size_t)xb * N, xv);
-    float2 lt = make_float2(0.f, 0.f);
+      for (int k = tid; k < nl; k += PINS_DDCG_TPB) __stcg(ug1 + lo + k, xv[k]);
+    csync();                                        // x slices published
+    spmv(ug1, xv);
+    float2 lt = zero;
     for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
       const float2 mx = ddv_add(ddv_mul(dg[k], xv[k]), od[k]);
-      od[k] = make_float2(0.f, 0.f);
+      od[k] = zero;
       const float2 t = ddv_add(split_f64(rhs_of(lo + k), shift), make_float2(-mx.x, -mx.y));
       rv[k] = t;
       acc2(lt, t, t);
     }
-    publish3(lt, make_float2(0.f, 0.f), make_float2(0.f, 0.f), buf);
-    cluster.sync();
+    publish3(lt, zero, zero, sb);
+    csync();
     float2 tt, d1, d2;
-    gather3(buf, tt, d1, d2);
+    gather3(sb, tt, d1, d2);
+    sb ^= 1;
     rr = tt;
     if (!(tt.x > 4.f * tol2 * bb.x)) break;         // within twice the tolerance
     conv = false;

@@ -129,6 +129,15 @@ __device__ __forceinline__ float2 ddv_axpy(float f, float2 v, float2 y) {
   float h, l; fast_two_sum(s, t, h, l);
   return make_float2(h, l);
 }
+// f v + y with f, v, y double-float (the product's f.y v.y term dropped)
+__device__ __forceinline__ float2 ddv_axpy2(float2 f, float2 v, float2 y) {
+  float p, e; two_prod(f.x, v.x, p, e);
+  e = __fmaf_rn(f.x, v.y, __fmaf_rn(f.y, v.x, e));
+  float s, t; two_sum(y.x, p, s, t);
+  t = __fadd_rn(t, __fadd_rn(y.y, e));
+  float h, l; fast_two_sum(s, t, h, l);
+  return make_float2(h, l);
+}
 // acc += v * u (v double-float, u FP32), unnormalised accumulation
 __device__ __forceinline__ void ddv_acc_mul(float2& acc, float2 v, float u) {
   float p, e; two_prod(v.x, u, p, e);

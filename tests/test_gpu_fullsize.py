@@ -173,10 +173,9 @@ def test_cg_at_8192_unknowns(gamma):
     gives ~10 000 entries per CTA, too many for shared memory, so the entries
     are read from the global scratch.  Both precisions reach the requested
     residual measured as ||M d - rhs|| (the mixed CG checks it and restarts
-    when its recurrences have drifted).  FP64 follows the oracle's PCG; the
-    mixed CG's pipelined ordering propagates rounding through its extra
-    recurrences and needs more iterations on these systems (2.6x on the
-    gamma = 2 one), so its count is bounded at 3x the oracle's."""
+    when its recurrences have drifted).  Both follow the oracle's textbook PCG
+    in exact arithmetic; FP64 within 2 % of its iteration count, the mixed CG
+    (double-float vectors, inner products and step lengths) within 5 %."""
     sysd = _stroke_system(gamma)
     rtol = 1e-6
     it_o = None
@@ -190,7 +189,7 @@ def test_cg_at_8192_unknowns(gamma):
             csr = po.CSR(m, n, ip.astype(np.int64), ix.astype(np.int64), data)
             _, _, it_o, _ = po.pcg(r, c, csr, eta, rhs[:m], rhs[m:], rtol=rtol, max_iter=20000)
         if prec == "mixed":
-            assert int(info[0]) <= 3 * it_o
+            assert abs(int(info[0]) - it_o) <= max(10, it_o // 20)
         else:
             assert abs(int(info[0]) - it_o) <= max(2, it_o // 50)
 
