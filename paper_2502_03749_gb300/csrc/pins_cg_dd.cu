@@ -48,7 +48,7 @@ namespace pins {
 
 #define PINS_DDCG_MAX 16
 #define PINS_DDCG_TPB 256
-#define PINS_DDCG_SMEM (200 * 1024)
+#define PINS_DDCG_SMEM (220 * 1024)
 // cluster size: one CTA up to PINS_DDCG_LOCAL_MAX unknowns (no exchange through
 // L2, no cluster barrier), else at most PINS_DDCG_SLICE unknowns per CTA where
 // the cluster size allows.  Measured on GB300: a 1-CTA CG on 512 unknowns takes
@@ -80,7 +80,8 @@ struct CGddArgs {
   float* ug;                       // exchange buffers: u, then x (2 N double-float pairs)
   size_t smem_bytes;               // dynamic shared memory of the launch
   double rtol2; int max_iter; double* info;
-  int* flag;                       // bit 0: an entry's target fell outside the cluster's slices
+  int* flag;                       // bit 0: an entry's target fell outside the cluster's slices;
+                                   // bit 7: a bulk-copy wait gave up
 };
 
 // longest slice a CTA of a cluster of cs may own: twice the uniform share when
@@ -95,7 +96,7 @@ __host__ __device__ inline int ddcg_slice_cap(int N, int cs) {
 // LOCAL: a cluster of one CTA holds every unknown, so the SpMV reads m from its
 // own shared memory and nothing goes through the exchange buffer.
 template <bool LOCAL>
-__global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
+__global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char ddcg_smem[];
   __shared__ float2 slot[2][3][PINS_DDCG_MAX];    // double-buffered block partials
@@ -189,16 +190,60 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // ---- own unknowns: diagonal, preconditioner, residual, row offsets ----
   const int E0 = beg(min(lo, N));
   const int E1 = beg(min(lo + nl, N));
-  // ---- entries of the own unknowns: packed (owner, offset) and value / eta, in
-  // shared memory when they fit, else in the global scratch ----
+  // ---- entries of the own unknowns: packed (target, value / eta, local row),
+  // in shared memory when they fit, else in the global scratch.  Thread t's
+  // SpMV share is the local entries [t ne / TPB, (t + 1) ne / TPB); its j-th
+  // entry is stored at slot j TPB + t, so one step of a warp reads contiguous
+  // words (conflict-free in shared memory, coalesced in global memory).
+  const int ne = E1 - E0;
+  const int c0 = (int)(((long long)tid * ne) / PINS_DDCG_TPB);
+  const int c1 = (int)(((long long)(tid + 1) * ne) / PINS_DDCG_TPB);
+  const size_t ent_slots = (size_t)((ne + PINS_DDCG_TPB - 1) / PINS_DDCG_TPB) * PINS_DDCG_TPB;
+  auto slot_of = [&](int le) -> int {
+    const int t = (int)((((long long)le + 1) * PINS_DDCG_TPB - 1) / ne);
+    const int ct = (int)(((long long)t * ne) / PINS_DDCG_TPB);
+    return (le - ct) * PINS_DDCG_TPB + t;
+  };
   const size_t used = base_bytes;
-  const bool ent_local = used + (2 * sizeof(int) + sizeof(float2)) * (size_t)(E1 - E0) <= a.smem_bytes;
+  const size_t ent_bytes_s = (2 * sizeof(int) + sizeof(float2)) * ent_slots;
+  const bool ent_local = used + ent_bytes_s <= a.smem_bytes;
   float2* ev_s = reinterpret_cast<float2*>(ddcg_smem + used);
-  int* et_s = reinterpret_cast<int*>(ev_s + (E1 - E0));
-  int* er_s = et_s + (E1 - E0);
-  int* etg = ent_local ? et_s : a.ent_tgt + E0;
-  float2* eva = ent_local ? ev_s : a.ent_val + E0;
-  int* erow = ent_local ? er_s : a.ent_row + E0;   // local unknown of each entry
+  int* et_s = reinterpret_cast<int*>(ev_s + ent_slots);
+  int* er_s = et_s + ent_slots;
+  const size_t gofs = (size_t)E0 + (size_t)rank * PINS_DDCG_TPB;   // padded global region
+  int* etg = ent_local ? et_s : a.ent_tgt + gofs;   // target - f0
+  float2* eva = ent_local ? ev_s : a.ent_val + gofs;
+  int* erow = ent_local ? er_s : a.ent_row + gofs;  // local unknown of each entry
+  // the targets this CTA reads lie in [f0, f1) (even bounds: 16-byte aligned
+  // copies); a cluster of one reads its own slice and keeps absolute targets
+  __shared__ unsigned int tmin_s[PINS_DDCG_TPB / 32], tmax_s[PINS_DDCG_TPB / 32];
+  int f0 = 0, f1 = N;
+  if (!LOCAL) {
+    unsigned int tmin = 0xffffffffu, tmax = 0u;
+    for (int e = E0 + tid; e < E1; e += PINS_DDCG_TPB) {
+      const int g = (e < Kc) ? m + __ldg(a.indices + e) : __ldg(a.rowidx + e - Kc);
+      if (g >= 0 && g < N) { tmin = min(tmin, (unsigned)g); tmax = max(tmax, (unsigned)g); }
+    }
+    tmin = __reduce_min_sync(0xffffffffu, tmin);
+    tmax = __reduce_max_sync(0xffffffffu, tmax);
+    if (lane == 0) { tmin_s[warp] = tmin; tmax_s[warp] = tmax; }
+    __syncthreads();
+    tmin = 0xffffffffu; tmax = 0u;
+    for (int w = 0; w < PINS_DDCG_TPB / 32; ++w) { tmin = min(tmin, tmin_s[w]); tmax = max(tmax, tmax_s[w]); }
+    if (tmin > tmax) { tmin = 0u; tmax = 0u; }     // no valid entry
+    f0 = (int)tmin & ~1;
+    f1 = ((int)tmax + 2) & ~1;                      // <= N + 1: inside the two exchange buffers
+  }
+  // a replica of the exchanged u[f0, f1) in shared memory, filled by bulk copies
+  // after each exchange, when the allocation has room after the slice and entries
+  const size_t rep_off = (used + (ent_local ? ent_bytes_s : 0) + 15) & ~(size_t)15;
+  const unsigned int rep_bytes = (unsigned int)((size_t)(f1 - f0) * sizeof(float2));
+  bool rep = !LOCAL && rep_off + rep_bytes <= a.smem_bytes &&
+             (reinterpret_cast<uintptr_t>(a.ug) & 15) == 0;
+  float2* ur = reinterpret_cast<float2*>(ddcg_smem + rep_off);
+  __shared__ __align__(8) unsigned long long rbar;
+  unsigned int rpar = 0;
+  if (rep && tid == 0) { mbar_init(&rbar, 1); fence_mbar_init(); }
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
     const int t = lo + k;
     const double d = (t < m) ? __ldg(a.r + t) : __ldg(a.c + t - m);
@@ -211,7 +256,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     od[k] = make_float2(0.f, 0.f);
     const int b0 = beg(t) - E0, b1 = beg(t + 1) - E0;
     rb[k] = b0;
-    for (int e = b0; e < b1; ++e) erow[e] = k;
+    for (int e = b0; e < b1; ++e) erow[slot_of(e)] = k;
   }
   if (tid == 0) rb[nl] = E1 - E0;
   for (int e = E0 + tid; e < E1; e += PINS_DDCG_TPB) {
@@ -221,10 +266,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     float2 val = ddv_mul(split_f64(v, 0), ie);
     if (g < 0 || g >= N) {
       atomicOr(a.flag, 1);
-      g = 0; val = make_float2(0.f, 0.f);
+      g = f0; val = make_float2(0.f, 0.f);
     }
-    etg[e - E0] = g;
-    eva[e - E0] = val;
+    const int sl = slot_of(e - E0);
+    etg[sl] = g - f0;
+    eva[sl] = val;
   }
   // first cluster barrier: every CTA has started (no distributed shared memory
   // access precedes it) and has published its block maximum
@@ -237,10 +283,6 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     rv[k] = split_f64(rhs_of(lo + k), shift);
     xv[k] = make_float2(0.f, 0.f);
   }
-  // entry-balanced slices of the SpMV: this thread takes [c0, c1) (relative to E0)
-  const int ne = E1 - E0;
-  const int c0 = (int)(((long long)tid * ne) / PINS_DDCG_TPB);
-  const int c1 = (int)(((long long)(tid + 1) * ne) / PINS_DDCG_TPB);
   __syncthreads();                                  // rb[], entries visible in the block
   int t0 = 0;                                       // last local unknown with rb <= c0
   if (c0 < c1) {
@@ -256,10 +298,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // start is its head (hrow), a row cut by its end its tail.  A tail is
   // completed from the heads of the following slices up to run_end (empty
   // slices, hrow = -2, contribute zero).
-  const int lastrow = (c0 < c1) ? erow[c1 - 1] : -1;
-  const bool single_run = (c0 < c1) && erow[c0] == lastrow;
+  const int lastrow = (c0 < c1) ? erow[(c1 - 1 - c0) * PINS_DDCG_TPB + tid] : -1;
+  const int firstrow = (c0 < c1) ? erow[tid] : -1;
+  const bool single_run = (c0 < c1) && firstrow == lastrow;
   const bool is_tail = (c0 < c1) && rb[lastrow + 1] > c1 && !(single_run && starts_mid);
-  hrow[tid] = (c0 < c1) ? (starts_mid ? erow[c0] : -1) : -2;
+  hrow[tid] = (c0 < c1) ? (starts_mid ? firstrow : -1) : -2;
   __syncthreads();
   int run_end = tid;
   if (is_tail)
@@ -273,11 +316,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   // Products first (independent), then a sum over runs of equal local row; a
   // row cut by the slice start is this thread's head, a row cut by its end its
   // tail (completed below from the following threads' heads, in thread order).
-  auto spmv = [&](const float2* src, const float2* lsrc) {
+  auto spmv = [&](const float2* src, const float2* lsrc, bool sm) {
     float2 headv = make_float2(0.f, 0.f), tailv = make_float2(0.f, 0.f);
     int headrow = -1, tailrow = -1;
     if (c0 < c1) {
-      int cur = erow[c0];
+      int cur = firstrow;
       bool first = true;
       float2 acc = make_float2(0.f, 0.f);
       for (int base = c0; base < c1; base += 4) {
@@ -285,12 +328,13 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const bool ok = base + q < c1;
-          tg[q] = ok ? etg[base + q] : 0;
-          v[q] = ok ? eva[base + q] : make_float2(0.f, 0.f);
-          rw[q] = ok ? erow[base + q] : cur;
+          const int sl = (base + q - c0) * PINS_DDCG_TPB + tid;
+          tg[q] = ok ? etg[sl] : 0;
+          v[q] = ok ? eva[sl] : make_float2(0.f, 0.f);
+          rw[q] = ok ? erow[sl] : cur;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) uu[q] = LOCAL ? lsrc[tg[q]] : __ldcg(src + tg[q]);
+        for (int q = 0; q < 4; ++q) uu[q] = sm ? lsrc[tg[q]] : __ldcg(src + tg[q]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           two_prod(v[q].x, uu[q].x, ph[q], pl[q]);
@@ -335,26 +379,32 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   };
   // three block partials (double-float) -> slot buffer `b` of every CTA (the
   // cluster barrier that follows publishes them)
+  auto shfl2 = [](float2 v, int o) -> float2 {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+  };
   auto warp_sum2 = [&](float2 v) -> float2 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float2 w = make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
-                                   __shfl_xor_sync(0xffffffffu, v.y, o));
-      v = ddv_add(v, w);
-    }
+    for (int o = 16; o > 0; o >>= 1) v = ddv_add(v, shfl2(v, o));
     return v;
   };
+  int CSP = 1;
+  while (CSP < CS) CSP <<= 1;
   auto norm2 = [](float2 v) { float h, l; fast_two_sum(v.x, v.y, h, l); return make_float2(h, l); };
   auto publish3 = [&](float2 v0, float2 v1, float2 v2, int b) {
     v0 = warp_sum2(norm2(v0)); v1 = warp_sum2(norm2(v1)); v2 = warp_sum2(norm2(v2));
     if (lane == 0) { red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; }
     __syncthreads();
     if (warp == 0) {
+      // every group of W lanes holds the W warp partials: after log2(W)
+      // butterfly levels every lane holds the same block total
       constexpr int W = PINS_DDCG_TPB / 32;
-      const float2 z = make_float2(0.f, 0.f);
-      float2 b0 = warp_sum2(lane < W ? red[0][lane] : z);
-      float2 b1 = warp_sum2(lane < W ? red[1][lane] : z);
-      float2 b2 = warp_sum2(lane < W ? red[2][lane] : z);
+      float2 b0 = red[0][lane & (W - 1)], b1 = red[1][lane & (W - 1)], b2 = red[2][lane & (W - 1)];
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) {
+        b0 = ddv_add(b0, shfl2(b0, o));
+        b1 = ddv_add(b1, shfl2(b1, o));
+        b2 = ddv_add(b2, shfl2(b2, o));
+      }
       if (lane < CS) {
         float2* rs = cluster.map_shared_rank(&slot[b][0][0], lane);
         rs[0 * PINS_DDCG_MAX + rank] = b0;
@@ -365,11 +415,19 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
   };
   // every warp sums the slots of buffer `b` in the same butterfly order
   // (bit-identical in all lanes and CTAs) and converts the totals to FP64
+  // (every group of CSP lanes, CSP the power of two >= CS, holds the CS slots
+  // and zeros, so log2(CSP) levels leave the same total in every lane)
   auto gather3 = [&](int b, float2& t0r, float2& t1r, float2& t2r) {
     const float2 z = make_float2(0.f, 0.f);
-    const float2 q0 = warp_sum2(lane < CS ? slot[b][0][lane] : z);
-    const float2 q1 = warp_sum2(lane < CS ? slot[b][1][lane] : z);
-    const float2 q2 = warp_sum2(lane < CS ? slot[b][2][lane] : z);
+    const int sl = lane & (CSP - 1);
+    float2 q0 = sl < CS ? slot[b][0][sl] : z;
+    float2 q1 = sl < CS ? slot[b][1][sl] : z;
+    float2 q2 = sl < CS ? slot[b][2][sl] : z;
+    for (int o = CSP >> 1; o > 0; o >>= 1) {
+      q0 = ddv_add(q0, shfl2(q0, o));
+      q1 = ddv_add(q1, shfl2(q1, o));
+      q2 = ddv_add(q2, shfl2(q2, o));
+    }
     t0r = q0; t1r = q1; t2r = q2;
   };
 
@@ -386,6 +444,27 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     if (LOCAL) __syncthreads(); else cluster.sync();
   };
   const float2 zero = make_float2(0.f, 0.f);
+  // ur <- the exchange buffer src (after the barrier that published it): bulk
+  // copies of up to 16 KB issued by thread 0, completed on rbar.  A wait that
+  // gives up (flag bit 7) ends the replica for this launch: the CTA returns to
+  // reading src through L2 and the caller poisons its partials, so that every
+  // CTA leaves the iteration.
+  bool rep_dead = false;
+  auto fetch = [&](const float2* src) -> bool {
+    if (tid == 0) {
+      asm volatile("fence.proxy.async;" ::: "memory");
+      mbar_expect_tx(&rbar, rep_bytes);
+      for (unsigned int off = 0; off < rep_bytes; off += 16384u)
+        bulk_g2s(reinterpret_cast<char*>(ur) + off, reinterpret_cast<const char*>(src) + off,
+                 min(16384u, rep_bytes - off), &rbar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&rbar, rpar, 1u << 22));
+    if (ok) { rpar ^= 1u; return true; }
+    if (tid == 0) atomicOr(a.flag, 128);
+    rep = false;
+    rep_dead = true;
+    return false;
+  };
 
   // Passes: PCG from (x, r) until the recurrence residual meets the tolerance;
   // then the true residual rhs - M x is formed (one more exchange and SpMV).  If
@@ -406,12 +485,16 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
       pv[k] = zero;
       if (!LOCAL) __stcg(ug0 + lo + k, u0);
     }
-    float2 gam_prev = make_float2(1.f, 0.f), alpha_prev = gam_prev;
+    // the generic-proxy stores above are read by other CTAs' bulk copies
+    if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
+    float2 rgam_prev = make_float2(1.f, 0.f), ralp_prev = rgam_prev;
     int itr = 0;
     conv = false;
     while (true) {
       csync();                                      // every u slice published
-      spmv(ug0, uv);
+      bool poison = false;
+      if (rep) poison = !fetch(ug0 + f0);
+      spmv(ug0 + f0, LOCAL ? uv : ur, LOCAL || rep);
       // w = M u of the own unknowns and the (r.u, w.u, r.r) partials
       float2 lg = zero, ld = zero, lrr = zero;
       for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
@@ -423,6 +506,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
         acc2(ld, w, uk);
         acc2(lrr, rk, rk);
       }
+      if (poison) lrr = make_float2(__int_as_float(0x7fc00000), 0.f);
       publish3(lg, ld, lrr, sb);
       csync();                                      // partials published
       // scalars (identical in every CTA)
@@ -434,12 +518,15 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
       if (!(rr.x > tol2 * bb.x)) { conv = true; break; }
       if (!(rr.x == rr.x) || it >= a.max_iter) break;   // NaN or the cap stops
       // beta = gam / gam', alpha = gam / (dlt - beta gam / alpha'); the
-      // difference can cancel, so it is formed in double-float
-      const float2 beta = (itr == 0) ? zero : ddv_div(gam, gam_prev);
+      // difference can cancel, so it is formed in double-float.  1/gam' and
+      // 1/alpha' were formed in the previous iteration, off this path.
+      const float2 beta = (itr == 0) ? zero : ddv_mul(gam, rgam_prev);
       const float2 den = (itr == 0) ? dlt
-                                    : ddv_add(dlt, ddv_neg(ddv_div(ddv_mul(beta, gam), alpha_prev)));
+                                    : ddv_add(dlt, ddv_neg(ddv_mul(ddv_mul(beta, gam), ralp_prev)));
       const float2 alpha = ddv_div(gam, den);
       const float2 nalpha = ddv_neg(alpha);
+      rgam_prev = ddv_div(make_float2(1.f, 0.f), gam);
+      ralp_prev = ddv_div(make_float2(1.f, 0.f), alpha);
       // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
       // with double-float step lengths: rounding them to FP32 (relative 2^-24
       // per step) costs conjugacy fast enough that these systems stall
@@ -452,8 +539,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
         pv[k] = pk; sv[k] = sk; xv[k] = xk; rv[k] = rk; uv[k] = uk;
         if (!LOCAL) __stcg(ug0 + lo + k, uk);
       }
-      gam_prev = gam;
-      alpha_prev = alpha;
+      if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
       ++it;
       ++itr;
     }
@@ -463,7 +549,7 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     if (!LOCAL)
       for (int k = tid; k < nl; k += PINS_DDCG_TPB) __stcg(ug1 + lo + k, xv[k]);
     csync();                                        // x slices published
-    spmv(ug1, xv);
+    spmv(ug1 + f0, xv, LOCAL);
     float2 lt = zero;
     for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
       const float2 mx = ddv_add(ddv_mul(dg[k], xv[k]), od[k]);
@@ -481,6 +567,9 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB) k_pcg_dd(CGddArgs a) {
     if (!(tt.x > 4.f * tol2 * bb.x)) break;         // within twice the tolerance
     conv = false;
   }
+  // a replica copy left in flight by a wait that gave up is awaited (bounded)
+  // before the CTA's shared memory goes away
+  if (rep_dead) mbar_wait_bounded(&rbar, rpar, 1u << 22);
   const double scale = ldexp(1.0, shift);
   double dg0 = 0.0, dg1 = 0.0;                      // <rhs, x>, <ab, x> partials
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {

@@ -102,6 +102,9 @@ cudaError_t launch_pcg_cluster(int m, int n, double eta, const double* r, const 
 // Double-float CG of the mixed path (one cluster); *used = false when the
 // problem does not fit, and then nothing was launched.  rhs == NULL: the
 // right-hand side is (ab - (r; c)); dots != NULL receives <rhs, x>, <ab, x>.
+// ent_tgt / ent_val / ent_row hold 2 nnz + PINS_DDCG_ENTRY_PAD slots (each CTA
+// pads its entries to a whole number of steps of its 256 threads).
+#define PINS_DDCG_ENTRY_PAD (16 * 256)
 cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const double* c,
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,

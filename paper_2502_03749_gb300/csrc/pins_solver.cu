@@ -104,8 +104,9 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.sw.tcol = cv.take<int>(kcap); w.sw.tcval = cv.take<double>(kcap);
   w.sw.longseg = cv.take<int>(N); w.sw.nlong = cv.take<int>(1);
   w.fkey = cv.take<float>(PINS_FAST_CAP); w.fij = cv.take<unsigned long long>(PINS_FAST_CAP);
-  w.ent_tgt = cv.take<int>(2 * (size_t)kcap); w.ent_val = cv.take<float2>(2 * (size_t)kcap);
-  w.ent_row = cv.take<int>(2 * (size_t)kcap);
+  w.ent_tgt = cv.take<int>(2 * (size_t)kcap + PINS_DDCG_ENTRY_PAD);
+  w.ent_val = cv.take<float2>(2 * (size_t)kcap + PINS_DDCG_ENTRY_PAD);
+  w.ent_row = cv.take<int>(2 * (size_t)kcap + PINS_DDCG_ENTRY_PAD);
   w.cg_u = cv.take<float>(4 * (size_t)N);   // two buffers of N double-float pairs
   w.cg_part = cv.take<double>(3 * 64 + 8);
   w.scal = cv.take<double>(Solver::SC_ROWRES + t1cap + 8);
@@ -752,6 +753,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
           if (flag) {
             err_ = std::string((flag & 64) ? "kernel error flag (injected by the test hook)"
                                : (flag & 16) ? "a bulk-copy wait gave up in a Sinkhorn pass"
+                               : (flag & 128) ? "cg: a bulk-copy wait gave up"
                                : (flag & 32) ? "certificate: the spanning-forest build did not settle"
                                              : "cg: an index outside the cluster's slices was skipped") +
                    " (flag " + std::to_string(flag) + ")";
