@@ -33,6 +33,10 @@ import os
 # the oracle legs run single-threaded (the paper's setting); no effect on the GPU path
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
+# one hardware work queue per serving slot: with the runtime's default of 8
+# queues, the pool's 16 solver streams share queues and a short request waits
+# behind the kernels of a long one (process-local; read when CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import argparse  # noqa: E402
 import json  # noqa: E402
@@ -436,7 +440,8 @@ def run_ours_strokes(args):
                        "grid_sizes": [w.grid[0] for w in ws],
                        "l2_note": "grid costs are generated, not stored; L2 flushed (256 MiB "
                                   "write) between timed steps",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")},
             "latency": {"p50_s": float(np.percentile(lats, 50)),
                         "p99_s": float(np.percentile(lats, 99)),
                         "of": "completion - arrival, every timed request"},

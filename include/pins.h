@@ -181,7 +181,12 @@ pins_status pins_solve_batch(pins_handle* h, const pins_problem* p, int count,
 
 /* Serving: admits a request (inputs are copied before return) and returns a
  * ticket.  Requests run as device memory and in-flight slots free up, overlapped
- * on the device.  Errors: PINS_ERR_QUEUE_FULL, PINS_ERR_INVALID_ARG. */
+ * on the device.  Errors: PINS_ERR_QUEUE_FULL, PINS_ERR_INVALID_ARG.
+ * Each slot has its own stream.  The CUDA runtime maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 unless the environment
+ * says otherwise, read when the process first uses CUDA); with more slots than
+ * queues, a short request's kernels can wait behind a long one's in a shared
+ * queue, so a server sets it to at least max_inflight (32 at most). */
 pins_status pins_submit(pins_handle* h, const pins_problem* p, uint64_t* ticket);
 
 /* Serving: PINS_ERR_PENDING while the ticket runs; otherwise fills *r (F_out and

@@ -658,14 +658,23 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
                           const double* rhs, double* x, const double* ab, double* dots,
-                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, double rtol,
-                          int max_iter, double* info, int* flag, cudaStream_t st, bool* used) {
+                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, int nnz,
+                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
+                          bool* used) {
   *used = false;
   const int N = m + n;
   const int CS = ddcg_cluster_for(N, ddcg_max_cluster());
   const int L = ddcg_slice_cap(N, CS);
   if (ddcg_smem_bytes(N, CS) > PINS_DDCG_SMEM || L > 0xffff) return cudaSuccess;   // caller falls back
-  const size_t smem = PINS_DDCG_SMEM;   // the rest holds a copy of u and the entries when they fit
+  // dynamic shared memory: the slice, room for the entries (1.5x the even share
+  // plus 512) and, in a cluster, for a replica of half the unknowns -- not the
+  // whole allocation, so that CTAs of other kernels can share these SMs.  A CTA
+  // whose entries or replica do not fit reads them from global memory.
+  size_t smem = ddcg_smem_bytes(N, CS);
+  const size_t share = (size_t)2 * (size_t)(nnz > 0 ? nnz : 0) / (size_t)CS;
+  smem += (size_t)16 * ((share + share / 2 + 512 + PINS_DDCG_TPB - 1) / PINS_DDCG_TPB * PINS_DDCG_TPB);
+  if (CS > 1) smem += (size_t)8 * ((size_t)N / 2 + 64);
+  smem = std::min(smem, (size_t)PINS_DDCG_SMEM);
   CGddArgs a;
   a.m = m; a.n = n; a.inv_eta = 1.0 / eta;
   a.r = r; a.c = c; a.indptr = indptr; a.indices = indices; a.data = data;

@@ -449,6 +449,7 @@ struct PassArgs {
   float2 s_l2e;                           // s log2(e) as a pair
   dd kappa2_dd;                           // log2(e) kappa_dd
   const double* a; const double* b;
+  const double* la; const double* lb;     // log a, log b (mixed grid half-steps; else NULL)
   const float2* exp_table;                // 2^(q/1024) pairs (mixed)
   int* err;                               // bit 4: a bulk-copy wait gave up (may be NULL)
 };

@@ -41,10 +41,11 @@ __device__ __forceinline__ unsigned int key_order(float x) {
 // One set of launchers per (precision policy, cost kind).
 struct PassSet {
   bool mixed;
-  void (*row_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* F_out,
-                  double* out_res, cudaStream_t);
-  void (*col_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* G_out,
-                  cudaStream_t);
+  // the Sinkhorn half-steps return the number of kernels they launched
+  int (*row_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* F_out,
+                 double* out_res, cudaStream_t);
+  int (*col_lse)(const PassArgs&, const TileGeom&, const MergeWS&, double* G_out,
+                 cudaStream_t);
   void (*marg)(const PassArgs&, const TileGeom&, const MergeWS&, const TrialArgs*,
                double* r, double* c, double* out4, cudaStream_t);
   void (*cert)(const PassArgs&, const TileGeom&, const MergeWS&, const CertArgs&, bool colpass,
@@ -109,12 +110,14 @@ cudaError_t launch_pcg_dd(int m, int n, double eta, const double* r, const doubl
                           const int* indptr, const int* indices, const double* data,
                           const int* colptr, const int* rowidx, const double* cdata,
                           const double* rhs, double* x, const double* ab, double* dots,
-                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, double rtol,
-                          int max_iter, double* info, int* flag, cudaStream_t st, bool* used);
+                          int* ent_tgt, float2* ent_val, int* ent_row, float* ug, int nnz,
+                          double rtol, int max_iter, double* info, int* flag, cudaStream_t st,
+                          bool* used);
 void launch_prep(const double* F, const double* G, int m, int n, double eta, double s,
                  double* A64, double* B64, float2* Add, float2* Bdd, cudaStream_t st);
 void launch_trial_prep(const double* d, int m, int n, double scale, double* P64, double* Q64,
                        float2* Pdd, float2* Qdd, cudaStream_t st);
+void launch_log_ab(const double* a, const double* b, int m, int n, double* out, cudaStream_t st);
 void launch_grad(const double* a, const double* b, const double* r, const double* c, int m,
                  int n, double* g, cudaStream_t st);
 void launch_axpy_prep(double* F, double* G, const double* d, int m, int n, double alpha,

@@ -24,8 +24,25 @@ int sm_count() {
 
 template <int K> struct Launch {
   using P = PINS_POLICY<K>;
-  static void row_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* F_out,
-                      double* out_res, cudaStream_t st) {
+  // grid cost of the mixed policy: the separable two-stage half-step, when both
+  // measures share the s1 x s2 grid and the stage buffers fit (T in rowpart0,
+  // one residual slot per grid column in scal_row, a column of T in 48 KB of
+  // shared memory)
+  static bool grid_separable(const PassArgs& p, int& s1, int& s2) {
+    s2 = p.cost.s2;
+    s1 = s2 > 0 ? p.m / s2 : 0;
+    return K == COST_GRID && P::MIXED && s2 > 0 && p.m == p.n && s1 * s2 == p.m &&
+           s2 <= 8 * PINS_GY_MAX && s1 <= 6144;
+  }
+  static int row_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* F_out,
+                     double* out_res, cudaStream_t st) {
+    int s1, s2;
+    if (grid_separable(p, s1, s2)) {
+      k_grid_lse1<true><<<s1, PINS_TPB, sizeof(float2) * s2, st>>>(p, s1, s2, ws.rowpart0);
+      k_grid_lse2<true><<<s2, PINS_TPB, sizeof(float2) * s1, st>>>(p, s1, s2, ws.rowpart0, ws,
+                                                                     F_out, out_res);
+      return 2;
+    }
     if constexpr (P::MIXED) {
       // column segments of ~1024 (at most g.gx of them: rowpart0 holds g.gx * m),
       // row groups for ~4 CTAs per SM (at most PINS_ROW_GROUPS counters)
@@ -44,13 +61,21 @@ template <int K> struct Launch {
         const int gy = std::max(1, std::min({(per_sm * sm_count() + sx - 1) / sx, PINS_ROW_GROUPS,
                                              (p.m + PINS_WARPS - 1) / PINS_WARPS}));
         k_row_lse_mx<P><<<dim3(sx, gy), PINS_TPB, smem, st>>>(p, seg, ws, F_out, out_res);
-        return;
+        return 1;
       }
     }
     k_row_lse<P><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, F_out, out_res);
+    return 1;
   }
-  static void col_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* G_out,
-                      cudaStream_t st) {
+  static int col_lse(const PassArgs& p, const TileGeom& g, const MergeWS& ws, double* G_out,
+                     cudaStream_t st) {
+    int s1, s2;
+    if (grid_separable(p, s1, s2)) {
+      k_grid_lse1<false><<<s1, PINS_TPB, sizeof(float2) * s2, st>>>(p, s1, s2, ws.rowpart0);
+      k_grid_lse2<false><<<s2, PINS_TPB, sizeof(float2) * s1, st>>>(p, s1, s2, ws.rowpart0, ws,
+                                                                      G_out, nullptr);
+      return 2;
+    }
     if constexpr (P::MIXED) {
       // row blocks for ~4 CTAs per SM, at most g.gy (colpart0 holds g.gy * n), and
       // enough of them for a block's A_i to fit in shared memory
@@ -65,10 +90,11 @@ template <int K> struct Launch {
             k_col_lse_mx<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, PINS_ROW_SEG_SMEM);
         (void)configured;
         k_col_lse_mx<P><<<dim3(g.gx, gy), PINS_TPB, smem, st>>>(p, rb, ws, G_out);
-        return;
+        return 1;
       }
     }
     k_col_lse<P><<<dim3(g.gx, g.gy), PINS_TPB, 0, st>>>(p, g, ws, G_out);
+    return 1;
   }
   static void marg(const PassArgs& p, const TileGeom& g, const MergeWS& ws, const TrialArgs* tr,
                    double* r, double* c, double* out4, cudaStream_t st) {

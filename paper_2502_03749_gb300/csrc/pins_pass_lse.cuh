@@ -105,7 +105,7 @@ k_row_lse(PassArgs p, TileGeom g, MergeWS ws, double* F_out, double* out_res) {
         const double lse = M + log(S);
         const double A = P::MIXED ? (double)p.Add[i].x + (double)p.Add[i].y : p.A64[i];
         const double ai = p.a[i];
-        res += fabs(exp(A + lse) - ai);
+        if (out_res) res += fabs(exp(A + lse) - ai);
         F_out[i] = p.eta * (log(ai) + p.s - lse);
       }
       __syncthreads();
@@ -113,7 +113,7 @@ k_row_lse(PassArgs p, TileGeom g, MergeWS ws, double* F_out, double* out_res) {
     const double br = block_sum(res, sh_red);
     if (threadIdx.x == 0) ws.scal_row[blockIdx.y] = br;
   }
-  if (arrive_last(ws.cnt_all, g.gx * g.gy)) {
+  if (out_res && arrive_last(ws.cnt_all, g.gx * g.gy)) {   // residual only when asked for
     const double v = ((int)threadIdx.x < g.gy) ? __ldcg(ws.scal_row + threadIdx.x) : 0.0;
     const double t = block_sum(v, sh_red);
     if (threadIdx.x == 0 && out_res) *out_res = t;

@@ -255,13 +255,15 @@ k_row_lse_mx(PassArgs p, int seg, MergeWS ws, double* F_out, double* out_res) {
       const double lse2 = (double)Mf + log2((double)Sf);         // base-2 LSE_j of w
       const double A2 = (p.F[i] * p.inv_eta - p.s) * 1.4426950408889634074;
       const double ai = p.a[i];
-      res += fabs(exp2(A2 + lse2) - ai);
+      if (out_res) res += fabs(exp2(A2 + lse2) - ai);
       F_out[i] = p.eta * (log(ai) + p.s - LN2 * lse2);
     }
     const double br = block_sum(res, sh_red);
     if (threadIdx.x == 0) ws.scal_row[y] = br;
   }
-  if (arrive_last(ws.cnt_all, SX * GY)) {
+  // the residual (read by the caller only at the end of a block of iterations)
+  // is skipped, with its FP64 exp2 per row, when out_res is NULL
+  if (out_res && arrive_last(ws.cnt_all, SX * GY)) {
     double v = 0.0;
     for (int q = threadIdx.x; q < GY; q += PINS_TPB) v += __ldcg(ws.scal_row + q);
     const double t = block_sum(v, sh_red);

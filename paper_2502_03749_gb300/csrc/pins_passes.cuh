@@ -122,6 +122,7 @@ __device__ __forceinline__ float2 as_f2(double v) { return *reinterpret_cast<flo
 
 #include "pins_pass_lse.cuh"
 #include "pins_pass_lse_mx.cuh"
+#include "pins_pass_grid_lse.cuh"
 #include "pins_pass_marg.cuh"
 #include "pins_pass_marg_mx.cuh"
 #include "pins_pass_cert.cuh"

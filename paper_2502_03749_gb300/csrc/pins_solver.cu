@@ -64,6 +64,7 @@ void carve(Carver& cv, Workspace& w, int m, int n, int kcap, int t1cap, const Ti
   w.rt = cv.take<double>(m); w.ct = cv.take<double>(n);
   w.Pt64 = cv.take<double>(m); w.Qt64 = cv.take<double>(n);
   w.grad = cv.take<double>(N); w.dir = cv.take<double>(N);
+  w.lab = cv.take<double>(N);
   w.cg_res = cv.take<double>(N); w.cg_p = cv.take<double>(N); w.cg_q = cv.take<double>(2 * (size_t)N);
   w.ab = cv.take<double>(N);
   w.xs = cv.take<double>(m); w.u = cv.take<double>(m); w.rr = cv.take<double>(m);
@@ -404,6 +405,7 @@ pins_status Solver::upload(const pins_problem& p) {
       break;
     }
     case PINS_COST_GRID_SQEUCLID:
+      if (mixed_) { launch_log_ab(a_, b_, p.m, p.n, ws_.lab, stream_); ++launches_; }
       break;
   }
   return check("upload");
@@ -431,6 +433,9 @@ PassArgs Solver::args(double s, const double* F, const double* G) {
   a.kappa2_dd.hi = (float)k2;
   a.kappa2_dd.lo = (float)(k2 - (double)a.kappa2_dd.hi);
   a.a = a_; a.b = b_;
+  const bool lab = mixed_ && cost_.kind == COST_GRID;
+  a.la = lab ? ws_.lab : nullptr;
+  a.lb = lab ? ws_.lab + m_ : nullptr;
   a.exp_table = exp_table_;
   a.err = reinterpret_cast<int*>(ws_.scal + SC_FLAG);
   return a;
@@ -446,7 +451,7 @@ void Solver::prep(double s) {
   ++launches_;
 }
 
-void Solver::sinkhorn_iter(double s, int t) {
+void Solver::sinkhorn_iter(double s, int t, bool with_res) {
   // the streamed mixed passes form their potentials from F, G themselves; Add/Bdd
   // are refreshed by the next prep() before any other pass.  Sizes whose row
   // segment or row block does not fit in shared memory use the tiled kernels,
@@ -458,13 +463,13 @@ void Solver::sinkhorn_iter(double s, int t) {
   refresh();
   PassArgs pa = args(s, ws_.F, ws_.G);
   prof_begin(PC_ROW_LSE);
-  ps_->row_lse(pa, geom_, ws_.mws, ws_.F, ws_.scal + SC_ROWRES + t, stream_);
+  launches_ += ps_->row_lse(pa, geom_, ws_.mws, ws_.F,
+                            with_res ? ws_.scal + SC_ROWRES + t : nullptr, stream_);
   prof_end();
   refresh();
   prof_begin(PC_COL_LSE);
-  ps_->col_lse(pa, geom_, ws_.mws, ws_.G, stream_);
+  launches_ += ps_->col_lse(pa, geom_, ws_.mws, ws_.G, stream_);
   prof_end();
-  launches_ += 2;
 }
 
 void Solver::marg(double s, bool trial, double alpha) {
@@ -650,7 +655,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
           cudaGraph_t graph = nullptr;
           const long long l0 = launches_;
           if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q);
+            for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q, q == blk - 1);
             if (cudaStreamEndCapture(stream_, &graph) != cudaSuccess ||
                 cudaGraphInstantiate(&gexec, graph, 0) != cudaSuccess)
               gexec = nullptr;
@@ -666,7 +671,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         }
       }
       if (!launched)
-        for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q);
+        for (int q = 0; q < blk; ++q) sinkhorn_iter(s, q, blk == check_every && q == blk - 1);
       t += blk;
       if (blk == check_every) {
         cudaMemcpyAsync(h_scal_ + SC_ROWRES + blk - 1, ws_.scal + SC_ROWRES + blk - 1,
@@ -707,7 +712,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
       }
       // M d = grad with grad = (a - r; b - c); also <grad, d> and <ab, d> for the line search
       cudaError_t ce = run_cg(mixed_, m, n, eta_, ws_.r, ws_.c, ws_.sw.indptr, ws_.sw.indices,
-                              ws_.sw.data, nullptr, ws_.dir, cfg.cg_rtol, max_cg,
+                              ws_.sw.data, keep, nullptr, ws_.dir, cfg.cg_rtol, max_cg,
                               ws_.scal + SC_CG, ws_.ab, ws_.scal + SC_DOTS);
       if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); r.status = PINS_ERR_CUDA; return PINS_ERR_CUDA; }
       bool accepted = false, redo = false;
@@ -785,7 +790,7 @@ pins_status Solver::solve(const pins_config& cfg, const pins_problem& p, pins_re
         zmax = h_scal_[SC_TRIAL + 2];
       } else {
         ++r.ls_failures;
-        sinkhorn_iter(s, 0);
+        sinkhorn_iter(s, 0, false);
         prep(s);
         marg(s, false);
         cudaMemcpyAsync(h_scal_ + SC_MARG, ws_.scal + SC_MARG, 4 * sizeof(double),
@@ -896,8 +901,9 @@ pins_status Solver::step_sparsify(const pins_config& cfg, const pins_problem& p,
 
 cudaError_t Solver::run_cg(bool mixed, int m, int n, double eta, const double* r,
                            const double* c, const int* indptr, const int* indices,
-                           const double* data, const double* rhs, double* d, double rtol,
-                           int max_iter, double* info, const double* ab, double* dots) {
+                           const double* data, int nnz, const double* rhs, double* d,
+                           double rtol, int max_iter, double* info, const double* ab,
+                           double* dots) {
   prof_begin(PC_CG);
   if (mixed) {
     // the double-float kernel forms rhs = ab - (r; c) itself when rhs is NULL and
@@ -905,7 +911,7 @@ cudaError_t Solver::run_cg(bool mixed, int m, int n, double eta, const double* r
     bool used = false;
     cudaError_t ce = launch_pcg_dd(m, n, eta, r, c, indptr, indices, data, ws_.sw.colptr,
                                    ws_.sw.rowidx, ws_.sw.cdata, rhs, d, ab, dots, ws_.ent_tgt,
-                                   ws_.ent_val, ws_.ent_row, ws_.cg_u, rtol, max_iter, info,
+                                   ws_.ent_val, ws_.ent_row, ws_.cg_u, nnz, rtol, max_iter, info,
                                    reinterpret_cast<int*>(ws_.scal + SC_FLAG), stream_, &used);
     if (used) { prof_end(); ++launches_; return ce; }
   }
@@ -937,7 +943,7 @@ pins_status Solver::step_cg(int m, int n, double eta, const double* r, const dou
   if (st != PINS_OK) return st;
   build_csc_from_csr(indptr, indices, data, m, n, nnz, ws_.sw, stream_);
   cudaMemsetAsync(ws_.scal + SC_FLAG, 0, sizeof(double), stream_);   // index-check flag
-  cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, rhs, d, rtol,
+  cudaError_t ce = run_cg(mixed, m, n, eta, r, c, indptr, indices, data, nnz, rhs, d, rtol,
                           max_iter, info, nullptr, nullptr);
   launches_ += 6;
   if (ce != cudaSuccess) { err_ = std::string("cg launch: ") + cudaGetErrorString(ce); return PINS_ERR_CUDA; }

@@ -18,6 +18,7 @@ struct Workspace {
   // potentials and vectors (FP64)
   double *F, *G, *Phi, *Psi, *A64, *B64, *r, *c, *rt, *ct, *Pt64, *Qt64;
   double *grad, *dir, *cg_res, *cg_p, *cg_q, *ab;
+  double* lab;                                  // (log a; log b): mixed grid half-steps
   double *xs, *u, *rr, *cr, *cp, *tc, *u2, *ys, *ec, *c1, *v;
   double *uT, *vT, *u2T;   // support-tree dual of the certificate
   TreeWS tw;
@@ -101,7 +102,7 @@ class Solver {
   // it fits, else the FP64 kernels).  rhs == NULL: rhs = (a - r; b - c).  dots
   // (may be NULL) receives <rhs, d> and <ab, d>.
   cudaError_t run_cg(bool mixed, int m, int n, double eta, const double* r, const double* c,
-                     const int* indptr, const int* indices, const double* data,
+                     const int* indptr, const int* indices, const double* data, int nnz,
                      const double* rhs, double* d, double rtol, int max_iter, double* info,
                      const double* ab, double* dots);
   long long launches() const { return launches_; }
@@ -131,7 +132,8 @@ class Solver {
   pins_status check(const char* where);
   pins_status sync(const char* where);
   void prep(double s);
-  void sinkhorn_iter(double s, int t);
+  // with_res: also form the row residual into SC_ROWRES + t (else skipped)
+  void sinkhorn_iter(double s, int t, bool with_res = true);
   void marg(double s, bool trial, double alpha = 0.0);
   pins_status sparsify(double s, int keep, double zmax, int* nnz_out, bool csc = true);
   // one-pass selection for the later Newton steps of an outer iteration (mixed);

@@ -549,6 +549,16 @@ void launch_grad(const double* a, const double* b, const double* r, const double
   k_grad<<<blocks, 256, 0, st>>>(a, b, r, c, m, n, g);
 }
 
+// (log a; log b), once per bound problem
+__global__ void k_log_ab(const double* a, const double* b, int m, int n, double* out) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m + n; t += gridDim.x * blockDim.x)
+    out[t] = log((t < m) ? a[t] : b[t - m]);
+}
+void launch_log_ab(const double* a, const double* b, int m, int n, double* out, cudaStream_t st) {
+  int N = m + n; int blocks = (N + 255) / 256; if (blocks > 512) blocks = 512;
+  k_log_ab<<<blocks, 256, 0, st>>>(a, b, m, n, out);
+}
+
 // (F, G) += alpha d
 // (F; G) += alpha d, then A = F/eta - s, B = G/eta (as k_prep) in the same launch
 __global__ void k_axpy_prep(double* F, double* G, const double* d, int m, int n, double alpha,

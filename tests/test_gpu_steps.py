@@ -108,6 +108,78 @@ def test_sinkhorn_half_steps(handles, prec, m, n):
                                atol=1e-14 if prec == "fp64" else 2e-7)
 
 
+GRIDS = [(7, 9), (16, 16), (1, 40), (33, 1), (48, 20), (64, 64)]
+
+
+def _grid_state(s1, s2, seed, eta):
+    """Dirichlet marginals on an s1 x s2 grid, squared grid distance / max, and
+    potentials a few eta away from zero."""
+    from paper_2502_03749_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    m = s1 * s2
+    a, b = rng.dirichlet(np.ones(m)), rng.dirichlet(np.ones(m))
+    scale = 1.0 / max(1, (s1 - 1) ** 2 + (s2 - 1) ** 2)
+    w = wl.Problem("grid", a, b, eta, cost_scale=scale, grid=(s1, s2))
+    F, G = rng.normal(size=m) * 2 * eta, rng.normal(size=m) * 2 * eta
+    return w, F, G
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("s1,s2", GRIDS)
+def test_sinkhorn_half_steps_grid(handles, prec, s1, s2):
+    """Grid costs generated on the fly.  The mixed path forms each half-step's
+    log-sum-exp in two separable stages (over the grid's rows, then its
+    columns); both paths against the oracle on the dense cost."""
+    import torch
+    eta, s = 0.05, 3.0
+    w, F, G = _grid_state(s1, s2, s1 * 101 + s2, eta)
+    C = w.dense_cost()
+    h = handles[prec]
+    ad, bd = dev(w.a), dev(w.b)
+    prob = pins.make_problem("grid", ad, bd, cost_scale=w.cost_scale, grid=w.grid, on_device=True)
+    Fd, Gd = dev(F), dev(G)
+    rr = torch.zeros(3, dtype=torch.float64, device="cuda")
+    st = pins.pins_step_sinkhorn(h.h, prob.prob, s, 3, Fd, Gd, rr)
+    assert st == 0, h.error()
+    Fo, Go, res = F.copy(), G.copy(), []
+    for _ in range(3):
+        Fo, rres = po.sinkhorn_row_step(C, w.a, Fo, Go, eta, s)
+        Go = po.sinkhorn_col_step(C, w.b, Fo, Go, eta, s)
+        res.append(rres)
+    atol = 1e-11 if prec == "fp64" else 2e-6 * eta
+    np.testing.assert_allclose(Fd.cpu().numpy(), Fo, atol=atol, rtol=0)
+    np.testing.assert_allclose(Gd.cpu().numpy(), Go, atol=atol, rtol=0)
+    np.testing.assert_allclose(rr.cpu().numpy(), res, rtol=1e-9 if prec == "fp64" else 1e-4,
+                               atol=1e-14 if prec == "fp64" else 2e-7)
+
+
+def test_sinkhorn_grid_at_the_benchmark_scale():
+    """64 x 64 grid at the benchmark's eta = 2.5e-4 and s = 20 (s / eta = 8e4):
+    most terms of a row underflow, the kept ones span the full FP32 range of
+    2^(w - M).  One mixed iteration against the oracle."""
+    import torch
+    eta, s = 2.5e-4, 20.0
+    w, F, G = _grid_state(64, 64, 77, eta)
+    C = w.dense_cost()
+    h = pins.Pins(prec="mixed", eta=eta)
+    try:
+        ad, bd = dev(w.a), dev(w.b)
+        prob = pins.make_problem("grid", ad, bd, cost_scale=w.cost_scale, grid=w.grid,
+                                 on_device=True)
+        Fd, Gd = dev(F), dev(G)
+        rr = torch.zeros(1, dtype=torch.float64, device="cuda")
+        st = pins.pins_step_sinkhorn(h.h, prob.prob, s, 1, Fd, Gd, rr)
+        assert st == 0, h.error()
+        Fg, Gg, rg = Fd.cpu().numpy(), Gd.cpu().numpy(), rr.cpu().numpy()
+    finally:
+        h.close()
+    Fo, rres = po.sinkhorn_row_step(C, w.a, F, G, eta, s)
+    Go = po.sinkhorn_col_step(C, w.b, Fo, G, eta, s)
+    np.testing.assert_allclose(Fg, Fo, atol=2e-6 * eta, rtol=0)
+    np.testing.assert_allclose(Gg, Go, atol=2e-6 * eta, rtol=0)
+    assert rg[0] == pytest.approx(rres, rel=1e-4, abs=2e-7)
+
+
 @pytest.mark.parametrize("m,n", [(300, 2048), (1030, 4096)])
 def test_sinkhorn_bulk_copy_segments(handles, m, n):
     """Dense FP32 costs whose width is a multiple of 1024 take the row pass that
