@@ -86,11 +86,21 @@ struct CGddArgs {
 
 // longest slice a CTA of a cluster of cs may own: twice the uniform share when
 // the shared memory holds it (room for balancing by work), else the share
+// (even in a cluster: slice bounds are even, so that slices move in 16-byte
+// double-float pairs)
 __host__ __device__ inline int ddcg_slice_cap(int N, int cs) {
   const int Lu = (N + cs - 1) / cs;
   if (cs == 1) return Lu;
   const int L2 = 2 * Lu;
-  return ((size_t)PINS_DDCG_PER_UNKNOWN * ((L2 + 3) & ~3) + 16 <= PINS_DDCG_SMEM) ? L2 : Lu;
+  return ((size_t)PINS_DDCG_PER_UNKNOWN * ((L2 + 3) & ~3) + 16 <= PINS_DDCG_SMEM) ? L2
+                                                                                  : (Lu + 1) & ~1;
+}
+
+// cluster address of a shared-memory location of CTA `rank`
+__device__ __forceinline__ unsigned int ddcg_mapa(const void* p, unsigned int rank) {
+  unsigned int r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
 }
 
 // LOCAL: a cluster of one CTA holds every unknown, so the SpMV reads m from its
@@ -116,9 +126,9 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
     return (t < m) ? __ldg(a.indptr + t) : Kc + __ldg(a.colptr + t - m);
   };
   // Slices balanced by work: unknowns [b_k, b_{k+1}) go to CTA k, with b_k the
-  // first unknown whose cumulative cost (entries before it + PINS_DDCG_UW per
-  // unknown before it) reaches k/CS of the total, each slice at most Lcap long.
-  // Every CTA computes the same boundaries.
+  // first even unknown at or below the one whose cumulative cost (entries
+  // before it + PINS_DDCG_UW per unknown before it) reaches k/CS of the total,
+  // each slice at most Lcap long.  Every CTA computes the same boundaries.
   __shared__ int sbound[PINS_DDCG_MAX + 1];
   const int Lcap = ddcg_slice_cap(N, CS);
   if (warp == 0) {
@@ -131,14 +141,14 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
         const int mid = (lo_s + hi_s) >> 1;
         if ((long long)beg(mid) + (long long)PINS_DDCG_UW * mid >= target) hi_s = mid; else lo_s = mid + 1;
       }
-      bk = lo_s;
+      bk = lo_s & ~1;
     }
     if (lane < CS) sbound[lane] = bk;
     __syncwarp();
     if (lane == 0) {
       sbound[0] = 0;
       for (int k = 1; k < CS; ++k) {
-        const int lower = max(sbound[k - 1], N - (CS - k) * Lcap);
+        const int lower = (max(sbound[k - 1], N - (CS - k) * Lcap) + 1) & ~1;
         const int upper = sbound[k - 1] + Lcap;
         sbound[k] = min(max(sbound[k], lower), upper);
       }
@@ -244,6 +254,11 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
   __shared__ __align__(8) unsigned long long rbar;
   unsigned int rpar = 0;
   if (rep && tid == 0) { mbar_init(&rbar, 1); fence_mbar_init(); }
+  // replica geometry of this CTA, read by the others after the first barrier
+  __shared__ int rinfo[4];                          // f0, f1, replica offset, has replica
+  __shared__ int cf0[PINS_DDCG_MAX], cf1[PINS_DDCG_MAX], croff[PINS_DDCG_MAX];
+  __shared__ int push_s;
+  if (tid == 0) { rinfo[0] = f0; rinfo[1] = f1; rinfo[2] = (int)rep_off; rinfo[3] = rep ? 1 : 0; }
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
     const int t = lo + k;
     const double d = (t < m) ? __ldg(a.r + t) : __ldg(a.c + t - m);
@@ -277,6 +292,30 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
   cluster.sync();
   unsigned int E = 0u;
   for (int q = 0; q < CS; ++q) E = max(E, *cluster.map_shared_rank(eslot, q));
+  // Exchange by push: when every CTA of the cluster holds a replica, each CTA
+  // copies its new u slice, per consumer the part within the consumer's target
+  // range, straight into the consumers' replicas (shared-to-shared bulk copies
+  // completing on the consumer's rbar), instead of through L2 and a barrier.
+  // Bounds are even (16-byte pairs); a slice ending at an odd N sends one pair
+  // more, which lands past the last target the consumer reads.
+  if (warp == 0) {
+    int ok = 1;
+    if (lane < CS) {
+      const int* ri = cluster.map_shared_rank(rinfo, lane);
+      cf0[lane] = ri[0]; cf1[lane] = ri[1]; croff[lane] = ri[2]; ok = ri[3];
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) push_s = (!LOCAL && ok) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool push = push_s != 0;
+  // bytes this CTA receives per exchange: the parts of every slice in [f0, f1)
+  unsigned int push_expect = 0u;
+  if (push)
+    for (int q = 0; q < CS; ++q) {
+      const int s0 = max(sbound[q], f0), e1 = (min(sbound[q + 1], f1) + 1) & ~1;
+      if (e1 > s0) push_expect += 8u * (unsigned int)(e1 - s0);
+    }
   const int shift = (int)E - 1023;                  // max |rhs| 2^-shift in [1, 2)
   // r0 = rhs (scaled) and x0 = 0 for the first pass
   for (int k = tid; k < nl; k += PINS_DDCG_TPB) {
@@ -450,6 +489,34 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
   // reading src through L2 and the caller poisons its partials, so that every
   // CTA leaves the iteration.
   bool rep_dead = false;
+  // push: each thread's u stores are ordered before the copy engine reads them,
+  // then lane c of warp 0 sends consumer c its part
+  auto push_out = [&]() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid < CS) {
+      const int c = tid;
+      const int s0 = max(lo, cf0[c]), e1 = (min(lo + nl, cf1[c]) + 1) & ~1;
+      if (e1 > s0) {
+        const unsigned int dst = ddcg_mapa(ddcg_smem + croff[c] + 8 * (s0 - cf0[c]), (unsigned)c);
+        const unsigned int bar = ddcg_mapa(&rbar, (unsigned)c);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            ::"r"(dst), "r"(smem_u32(uv + (s0 - lo))), "r"(8u * (unsigned int)(e1 - s0)), "r"(bar)
+            : "memory");
+      }
+    }
+  };
+  // push: wait until every part of this exchange has arrived (bounded; a wait
+  // that gives up sets flag bit 7 and the caller poisons its partials)
+  auto push_in = [&]() -> bool {
+    if (tid == 0) mbar_expect_tx(&rbar, push_expect);
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&rbar, rpar, 1u << 22));
+    if (ok) { rpar ^= 1u; return true; }
+    if (tid == 0) atomicOr(a.flag, 128);
+    rep_dead = true;
+    return false;
+  };
   auto fetch = [&](const float2* src) -> bool {
     if (tid == 0) {
       asm volatile("fence.proxy.async;" ::: "memory");
@@ -483,17 +550,22 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
       uv[k] = u0;
       sv[k] = zero;
       pv[k] = zero;
-      if (!LOCAL) __stcg(ug0 + lo + k, u0);
+      if (!LOCAL && !push) __stcg(ug0 + lo + k, u0);
     }
     // the generic-proxy stores above are read by other CTAs' bulk copies
-    if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (push) push_out();
+    else if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
     float2 rgam_prev = make_float2(1.f, 0.f), ralp_prev = rgam_prev;
     int itr = 0;
     conv = false;
     while (true) {
-      csync();                                      // every u slice published
       bool poison = false;
-      if (rep) poison = !fetch(ug0 + f0);
+      if (push) {
+        poison = rep_dead || !push_in();            // every part of u in the replica
+      } else {
+        csync();                                    // every u slice published
+        if (rep) poison = !fetch(ug0 + f0);
+      }
       spmv(ug0 + f0, LOCAL ? uv : ur, LOCAL || rep);
       // w = M u of the own unknowns and the (r.u, w.u, r.r) partials
       float2 lg = zero, ld = zero, lrr = zero;
@@ -537,9 +609,10 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
         const float2 rk = ddv_axpy2(nalpha, sk, rv[k]);
         const float2 uk = ddv_scale(dinv[k], rk);
         pv[k] = pk; sv[k] = sk; xv[k] = xk; rv[k] = rk; uv[k] = uk;
-        if (!LOCAL) __stcg(ug0 + lo + k, uk);
+        if (!LOCAL && !push) __stcg(ug0 + lo + k, uk);
       }
-      if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
+      if (push) push_out();
+      else if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
       ++it;
       ++itr;
     }
