@@ -192,7 +192,7 @@ EX2_PEAK_GPS = SMS * MUFU_PER_SM * SM_GHZ                          # G ex2 per s
 # the class's kernel on the roofline's workload (profiles/); remove an entry
 # once its kernel changes after the capture.
 NCU_TRAFFIC_BYTES = {
-    "cg": None,              # k_pcg_dd changed since its last capture
+    "cg": 663552 + 0,        # k_pcg_dd, 64 x 64 stroke pair (profiles/k_pcg_dd_stroke64.md)
 }
 
 
@@ -221,7 +221,7 @@ def roofline(prof, m, n, elem_bytes, cg_iters, nnz, peaks, streamed):
                 "peak_source": "derived: FP32 units x clock (152 x 128 x 2 x 2.07 GHz)",
                 "work": "4 nnz + 14 (m + n) flops per CG iteration (the method's own work)",
                 "avg_launch_us": t * 1e6, "launches": cnt, "iters_per_launch": iters,
-                "note": "latency-bound: two cluster barriers and one exchange per CG iteration"}, dom
+                "note": "latency-bound: one exchange (pushed into the replicas) and one cluster barrier per CG iteration"}, dom
     if streamed:
         per_launch = float(m) * n
         achieved = per_launch / t / 1e9

@@ -18,7 +18,7 @@
 //
 // Ordering: the single-reduction PCG of Chronopoulos & Gear (J. Comput. Appl.
 // Math. 25, 1989), as in the FP64 cluster CG:
-//   u = D^-1 r published                                  [cluster barrier]
+//   u = D^-1 r exchanged                                  [arrival, or barrier]
 //   w = M u;  (r.u, w.u, r.r) partials published          [cluster barrier]
 //   gamma, delta, rr (every CTA, same order);  stop if rr <= rtol^2 rr_0
 //   beta = gamma/gamma', alpha = gamma/(delta - beta gamma/alpha')
@@ -32,10 +32,15 @@
 // pipelined iteration stalls where the textbook one converges, and here it
 // needed 2.6x the textbook iterations with restarts.  The single-reduction
 // form follows the textbook count within a few per cent at this precision.
-// The u slices go through L2 (one buffer: its reads and writes are separated by
-// a barrier each way), the block partials through distributed shared memory
-// (two alternating slot sets).  A system small enough for one CTA runs in a
-// cluster of one, which reads u from its own shared memory.
+// Each CTA keeps a replica of u over the range of targets its entries read.
+// When every CTA has room for its replica, each CTA pushes its new u slice into
+// the replicas with shared-to-shared bulk copies that complete on the
+// consumer's mbarrier, so the consumer waits for its data alone, not for a
+// cluster barrier; otherwise u goes through L2 (one buffer: its reads and
+// writes are separated by a barrier each way) and is fetched into the replica
+// or gathered from L2.  The block partials go through distributed shared
+// memory (two alternating slot sets).  A system small enough for one CTA runs
+// in a cluster of one, which reads u from its own shared memory.
 // Every CTA sums the block partials in the same order and takes the same
 // decisions, so results are reproducible run to run.
 #include <cooperative_groups.h>
@@ -597,8 +602,6 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
                                     : ddv_add(dlt, ddv_neg(ddv_mul(ddv_mul(beta, gam), ralp_prev)));
       const float2 alpha = ddv_div(gam, den);
       const float2 nalpha = ddv_neg(alpha);
-      rgam_prev = ddv_div(make_float2(1.f, 0.f), gam);
-      ralp_prev = ddv_div(make_float2(1.f, 0.f), alpha);
       // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r,
       // with double-float step lengths: rounding them to FP32 (relative 2^-24
       // per step) costs conjugacy fast enough that these systems stall
@@ -613,6 +616,9 @@ __global__ void __launch_bounds__(PINS_DDCG_TPB, 1) k_pcg_dd(CGddArgs a) {
       }
       if (push) push_out();
       else if (!LOCAL) asm volatile("fence.proxy.async.global;" ::: "memory");
+      // the next step's 1/gam' and 1/alpha', formed while the exchange is in flight
+      rgam_prev = ddv_div(make_float2(1.f, 0.f), gam);
+      ralp_prev = ddv_div(make_float2(1.f, 0.f), alpha);
       ++it;
       ++itr;
     }
