@@ -1,5 +1,6 @@
 """Host-side logic of bench.py that needs no GPU: the roofline object built from
-per-class timer totals, and the clock summary built from nvidia-smi samples."""
+per-class timer totals, the clock summary built from nvidia-smi samples, and
+the all-core oracle leg of the CPU baseline."""
 import os
 import sys
 
@@ -89,3 +90,18 @@ def test_clock_summary_takes_the_median_and_the_active_reasons():
 
 def test_clock_summary_without_samples_says_so():
     assert bench.ClockSampler().summary()["reasons"] == ["unsampled"]
+
+
+def test_all_core_oracle_leg_runs_full_certified_solves():
+    """The all-core CPU baseline: one oracle solve per core at a time in a
+    spawn-started pool; every solve reaches the certified gap."""
+    saved = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = saved
+    done, dt, gmax = bench.oracle_sample_cores(args, 0.0, 2)
+    assert done == 2 and dt > 0.0
+    assert gmax <= bench.TOL_GAP
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
