@@ -199,6 +199,33 @@ def test_armijo_rejects_ascent_violations():
     assert not ok and trials == 6
 
 
+@pytest.mark.parametrize("scale", [3.0, 40.0, 400.0])
+def test_armijo_accepts_the_largest_admissible_power_of_beta(scale):
+    """Algorithm 2 line search (beta = 0.5, c1 = 1e-4): the accepted alpha is
+    the largest beta^q whose sufficient-increase inequality holds, found here
+    by brute force over q on the directly evaluated dual objective; every
+    larger step violates it.  An ascent direction scaled up overshoots, so the
+    search backtracks several times before it accepts."""
+    m, n = 5, 7
+    C, a, b, eta = _rand_problem(m, n, 29, eta=0.2)
+    rng = np.random.default_rng(5)
+    F, G = rng.normal(size=m) * 0.05, rng.normal(size=n) * 0.05
+    s = 2.0
+    ga, gb, _, _ = po.gradient(C, a, b, F, G, eta, s)
+    df, dg = scale * ga, scale * gb
+    gtd = float(ga @ df + gb @ dg)
+    beta, c1, Q = 0.5, 1e-4, 30
+    P0 = po.dual_objective(C, a, b, F, G, eta, s)
+    ok_q = [po.dual_objective(C, a, b, F + beta ** q * df, G + beta ** q * dg, eta, s) - P0
+            >= c1 * beta ** q * gtd for q in range(Q + 1)]
+    q_star = ok_q.index(True)
+    alpha, ok, trials = po.armijo(C, a, b, F, G, eta, s, df, dg, gtd, beta, c1, Q)
+    assert ok and alpha == beta ** q_star and trials == q_star + 1
+    assert not any(ok_q[:q_star])
+    if scale >= 40.0:
+        assert q_star >= 2       # the search really backtracked
+
+
 # --------------------------------------------------------------------------- #
 # Certificate (reading R9)
 # --------------------------------------------------------------------------- #
